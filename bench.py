@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of the MPO Lindblad Trotter step on GB300.
+
+Workload (default ``chain20_chi256``): N=20 open chain with the seeded
+couplings of the precision-comparison model (J_b~U[0.05,0.15],
+Omega~U[0.3,0.7], g0_i~U[0.005,0.02], g2_i~U[0.01,0.03], h_z alternating 0,1),
+chi_max = 256 saturated from the first step (seeded random MPO start), cutoff
+1e-10, dt = 0.02, second-order Trotter: 29 two-site gate applications per step,
+18 of them on 1024 x 1024 bond matrices.
+
+A step = one mpdo_trotter_step(1) over the whole batch (merge, gate, weight,
+Jacobi SVD, truncation, reconstruction for every op, trace forcing).
+``value`` = gate applications per second (device-timed, inputs resident),
+``e2e`` = same through the C ABI with the state uploaded from host memory and
+observables read back each step.
+
+--gpus N > 1 runs N independent replicas (one per rank, launched by torchrun):
+the method has no exchange step between instances.
+``--impl reference`` times the CPU oracle (plain C Jacobi, one thread) on a
+bounded sample: each step is one 1024 x 1024 gate application.
+``--probe-peaks`` measures the FP64 / FP32 / TF32 GEMM rates with cuBLAS.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP64_PEAK_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (recipe table, nominal)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chain20_chi256")
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--probe-peaks", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+def make_workload(name):
+    import workloads as W
+    if name == "chain20_chi256":
+        wl = W.chain20_precision(chi_max=256)
+        dims, tens = W.random_mpo_state(wl.n, 256, seed=2203058712 + 1)
+        return wl, dims, tens, 256
+    if name == "chain20_chi128":
+        wl = W.chain20_precision(chi_max=128)
+        dims, tens = W.random_mpo_state(wl.n, 128, seed=2203058712 + 1)
+        return wl, dims, tens, 128
+    raise SystemExit(f"unknown workload {name}")
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+                self.out, _ = self.p.communicate()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"),
+                               f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(wl, dims, tens, reps, warm):
+    """Time the oracle on full-size (1024 x 1024) gate applications, one
+    thread.  Returns (seconds per op, description)."""
+    import numpy as np
+    from oracle import schedule, tebd
+    layers = schedule.step_layers(wl.n, wl.bonds)
+    gates = tebd.build_gates(wl, 0, layers, wl.dt)
+    st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
+    cap = int(wl.chi_max[0])
+    # the first op of the step whose bond matrix is (4 cap) x (4 cap)
+    pick = None
+    for L, gl in zip(layers, gates):
+        for op, G in zip(L, gl):
+            p = op[1]
+            if dims[p] == cap and dims[p + 2] == cap:
+                pick = (p, G)
+                break
+        if pick:
+            break
+    p, G = pick
+    times = []
+    for r in range(warm + reps):
+        s = st.copy()
+        t0 = time.perf_counter()
+        s.apply(p, G, cap, float(wl.cutoff[0]))
+        dt = time.perf_counter() - t0
+        if r >= warm:
+            times.append(dt)
+    return times, f"gate application on a {4 * cap}x{4 * cap} bond matrix (op at p={p}), plain C Jacobi"
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, dims, tens, cap = make_workload(args.workload)
+    times, what = oracle_sample(wl, dims, tens, args.steps, min(args.warmup, 1))
+    v = len(times) / sum(times)
+    line = {"impl": "reference", "metric": "gate_applications_per_sec", "value": v,
+            "unit": "gate-applications/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "oracle": "CPU FP64, one thread"},
+            "cpu_baseline": {"value": v, "unit": "gate-applications/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} x {what}"},
+            "e2e": {"value": v, "unit": "gate-applications/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def cpu_baseline_subprocess(args):
+    """Run the oracle sample in a child process with one BLAS thread."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env.pop("RANK", None)
+    env.pop("WORLD_SIZE", None)
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
+           "--workload", args.workload]
+    try:
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600).stdout
+        line = json.loads(out.strip().splitlines()[-1])
+        cb = line["cpu_baseline"]
+        cb["sample"] += " (1 op; no warm-up)"
+        return cb
+    except Exception as ex:  # baseline failure must not hide the GPU number
+        return {"value": None, "unit": "gate-applications/s", "cores": 1, "kind": "oracle",
+                "sample": f"failed: {ex}"}
+
+
+# ---------------------------------------------------------------------------
+def probe_peaks():
+    import torch
+    res = {}
+
+    def best(fn, it=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        b = 1e9
+        for _ in range(it):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            fn()
+            e.record()
+            torch.cuda.synchronize()
+            b = min(b, s.elapsed_time(e) / 1e3)
+        return b
+    torch.backends.cuda.matmul.allow_tf32 = False
+    for dt, n, key in [(torch.float64, 8192, "fp64_dgemm_tflops"), (torch.float32, 8192, "fp32_sgemm_tflops")]:
+        a = torch.randn(n, n, device="cuda", dtype=dt)
+        b = torch.randn(n, n, device="cuda", dtype=dt)
+        res[key] = 2 * n ** 3 / best(lambda: a @ b) / 1e12
+    torch.backends.cuda.matmul.allow_tf32 = True
+    a = torch.randn(8192, 8192, device="cuda")
+    b = torch.randn(8192, 8192, device="cuda")
+    res["tf32_gemm_tflops"] = 2 * 8192 ** 3 / best(lambda: a @ b) / 1e12
+    res["how"] = "torch.matmul 8192^3, best of 10, CUDA events"
+    print(json.dumps(res))
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.probe_peaks:
+        return probe_peaks()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    from paper_2203_05871_gb300 import Solver, build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    wl, dims, tens, cap = make_workload(args.workload)
+    stream = torch.cuda.Stream()
+    s = Solver(wl.n, batch=1, chi_cap=cap, stream=stream)
+    s.build_gates(wl)
+    s.set_state(0, dims, tens)
+    n_ops, n_swaps, _ = s.op_counts()
+    for _ in range(args.warmup):
+        s.step(1)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    s.profile(True)
+    s.profile_read(reset=True)
+    ms = 0.0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)                       # L2 flush between timed steps
+            torch.cuda.synchronize()
+            if dist:
+                dist.barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+    prof = s.profile_read(reset=True)
+    s.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * n_ops * args.steps / (ms / 1e3)
+    st = s.status()
+
+    # end to end through the C ABI from host buffers (state in, observables out)
+    flat_bytes = sum(int(np.asarray(t).size) for t in tens) * 8
+    e2e_ms = 0.0
+    for _ in range(args.e2e_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_state(0, dims, tens)
+        s.step(1)
+        z = s.measure_1q(range(wl.n), "Z")
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_value = world * n_ops * args.e2e_steps / (e2e_ms / 1e3)
+
+    jac = prof["jacobi_svd"]
+    achieved = jac["flops"] / (jac["ms"] / 1e3) / 1e12 if jac["ms"] > 0 else None
+    launches = sum(v["launches"] for v in prof.values())
+    line = {
+        "metric": "gate_applications_per_sec", "value": value, "unit": "gate-applications/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "s_per_trotter_step": ms_per_step / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "n_qubits": wl.n, "chi_max": cap, "cutoff": float(wl.cutoff[0]),
+                   "dt": wl.dt, "ops_per_step": n_ops, "swaps_per_step": n_swaps, "precision": args.precision,
+                   "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed steps",
+                   "start": "seeded random MPO at chi=256"},
+        "e2e": {"value": e2e_value, "unit": "gate-applications/s", "h2d_bytes_per_step": flat_bytes,
+                "d2h_bytes_per_step": wl.n * 8},
+        "gpu_launches": launches,
+        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
+                    for k, v in prof.items() if v["launches"]},
+        "roofline": {"kernel": "jacobi_svd", "bound": "alu", "achieved": achieved,
+                     "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
+                     "traffic": None,
+                     "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
+                             "FP64 of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)"},
+        "clocks": clk.summary(),
+        "status": int(st["status"][0]), "chi_max_seen": int(st["chi"].max()),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_subprocess(args)
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

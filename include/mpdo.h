@@ -1,0 +1,184 @@
+/*
+ * libmpdo -- MPO Lindblad-equation solver for one GB300 (sm_103a).
+ *
+ * Evolves the density matrix of N qubits, stored as a matrix product operator
+ * in the normalised Pauli basis P_a/sqrt(2), a in (I, X, Y, Z) (App. A,
+ * Eq. (mpo_def): the vectorised |rho>> is an MPS with local dimension 4),
+ * under the Lindblad equation of Sec. 2.1 (Eq. (dtrho), Eq. (H0),
+ * Eq. (K_def), Eqs. (D0)-(D2)), by second-order Trotter steps of two-site
+ * propagator gates exp(L_ij dt) with SVD truncation after every gate (App. B:
+ * the more severe of a relative discarded-weight cutoff and a maximum bond
+ * dimension).  Observables are the Pauli expectation values of Sec. 2.3,
+ * Eq. (mu) and Eq. (2Qdef), and the connected correlator of Eq. (etadef).
+ *
+ * Conventions
+ *  - Every function returns MPDO_OK (0) or a negative MPDO_E* code and never
+ *    aborts; mpdo_last_error() gives a message for the calling thread.
+ *  - Host arrays passed in are caller-owned and copied during the call.
+ *  - The context owns all device memory; it is allocated in mpdo_init (state
+ *    and measurement buffers, sized by chi_cap) and mpdo_build_gates (gates
+ *    and per-op workspaces, sized by the bond graph), never during a step.
+ *  - Work is ordered on the CUDA stream given to mpdo_init.  Calls that return
+ *    results in host memory synchronise that stream.
+ *  - Bond dimensions are dynamic (chosen by truncation on the device) and
+ *    bounded by each instance's chi_max <= chi_cap.
+ *  - The state is real: in the Pauli basis the Lindbladian of Sec. 2.1 maps
+ *    Hermitian operators to Hermitian operators, so the gate matrices and the
+ *    MPO coefficients are real (MPDO_STORE_F64 plays the role of complex128
+ *    storage, MPDO_STORE_F32 of complex64).
+ */
+#ifndef MPDO_H
+#define MPDO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpdo_ctx mpdo_ctx;
+
+/* return codes */
+enum {
+    MPDO_OK = 0,
+    MPDO_EINVAL = -1,      /* invalid argument (message says which) */
+    MPDO_ENOMEM = -2,      /* device or host allocation failed */
+    MPDO_ECUDA = -3,       /* a CUDA runtime call failed */
+    MPDO_ENOCONV = -4,     /* Jacobi SVD hit its sweep limit (some instance) */
+    MPDO_ETIMEOUT = -5,    /* a device-side wait gave up (kernel returned early) */
+    MPDO_ENONFINITE = -6,  /* NaN/Inf detected in some instance */
+    MPDO_ECAPACITY = -7,   /* requested size exceeds a capacity fixed at init */
+    MPDO_ESTATE = -8       /* call out of order (e.g. step before build_gates) */
+};
+
+/* per-instance status bits reported by mpdo_status */
+enum {
+    MPDO_ST_NOCONV = 1,
+    MPDO_ST_NONFINITE = 2,
+    MPDO_ST_TIMEOUT = 4,
+    MPDO_ST_CAPACITY = 8
+};
+
+/* contraction precision (merge, gate and reconstruct contractions) */
+enum { MPDO_FP64 = 0, MPDO_MIXED_TF32 = 1, MPDO_MIXED_BF16X3 = 2 };
+/* storage of the site tensors */
+enum { MPDO_STORE_F64 = 0, MPDO_STORE_F32 = 1 };
+
+typedef struct {
+    int n_qubits;            /* N >= 3 (Sec. 2.1 model; the paper's solver wants N > 2) */
+    int batch;               /* B >= 1 independent instances sharing one bond graph */
+    int chi_cap;             /* capacity bond dimension, >= every chi_max, <= 512 */
+    int precision;           /* MPDO_FP64 | MPDO_MIXED_TF32 | MPDO_MIXED_BF16X3 */
+    int storage;             /* MPDO_STORE_F64 | MPDO_STORE_F32 */
+    int trotter_order;       /* 2 (symmetric second-order product) */
+    int force_trace;         /* 1: rho /= tr rho after every step (App. B b_force_rho_trace) */
+    int jacobi_max_sweeps;   /* sweep limit of the Jacobi SVD (default 40) */
+    double jacobi_tol;       /* <= 0: sqrt(L) * DBL_EPSILON for rows of length L */
+    unsigned barrier_timeout_ms;  /* limit of every device-side wait (default 4000) */
+    int max_slots;           /* <= 0: automatic; else max two-site ops in flight */
+    int device;              /* CUDA device ordinal; < 0: the calling thread's current device */
+} mpdo_config;
+
+typedef struct {
+    /* per-instance model parameters, row-major [B][N] (h_y, g1 may be NULL = 0) */
+    const double *h_x, *h_y, *h_z;     /* on-site fields of Eq. (H0) */
+    const double *g0, *g1, *g2;        /* rates of Eqs. (D0), (D1), (D2), >= 0 */
+    int n_bonds;                       /* >= 1; every qubit must be on some bond */
+    const int *bond_i, *bond_j;        /* [n_bonds] qubits = positions on the MPO path */
+    const double *J, *Jz;              /* [B][n_bonds] couplings of Eq. (K_def); Jz may be NULL */
+    const int *chi_max;                /* [B] max bond dimension (App. B max_dim_rho) */
+    const double *cutoff;              /* [B] max relative discarded weight (App. B cut_off_rho) */
+    const char *init_pauli;            /* 2N chars, e.g. "+z+z-x" (Sec. 2.2); NULL = all "+z" */
+} mpdo_model;
+
+/* Fill *cfg with defaults (n_qubits, batch and chi_cap still to be set). */
+int mpdo_config_default(mpdo_config *cfg);
+
+/* Create a context: validates cfg, allocates every device buffer for
+ * chi_cap and the bond graph size given later (up to n_qubits).  cuda_stream
+ * is a cudaStream_t (NULL = legacy default stream) that all work is ordered on. */
+int mpdo_init(mpdo_ctx **out, const mpdo_config *cfg, void *cuda_stream);
+
+/* Build the op list of one Trotter step from the bond graph (even
+ * nearest-neighbour bonds, odd ones, then each long-range bond through swap
+ * gates; Sec. 2.5 maps any connectivity onto the 1D path), then build every
+ * two-site gate exp(L_op * f * dt) on the device (16x16, real, Pauli basis)
+ * and reset the state to the Pauli product state rho(t0) of Sec. 2.2.
+ * model arrays are host memory.  Errors: EINVAL (bad graph, negative rates,
+ * chi_max > chi_cap, malformed init string), ECUDA. */
+int mpdo_build_gates(mpdo_ctx *ctx, const mpdo_model *model, double dt);
+
+/* Advance every instance by n_steps second-order Trotter steps.  Per op:
+ * merge the two sites, apply the gate, weight by the left Schmidt values,
+ * SVD (FP64 one-sided Jacobi), truncate, write the two new sites.  After each
+ * step the trace is forced to 1 when cfg.force_trace.  Returns ENOCONV /
+ * ENONFINITE / ETIMEOUT when some instance reported that status (the other
+ * instances are still advanced), ESTATE before mpdo_build_gates. */
+int mpdo_trotter_step(mpdo_ctx *ctx, int n_steps);
+
+/* <sigma^comp_q> / tr rho for each q in qubits[nq] and each instance
+ * (Eq. (mu)); comp in 'X','Y','Z','I'.  out is [B][nq] doubles, a host
+ * pointer (out_on_device = 0; the call synchronises) or a device pointer. */
+int mpdo_measure_1q(mpdo_ctx *ctx, const int *qubits, int nq, char comp, double *out,
+                    int out_on_device);
+
+/* <sigma^comp[0]_i sigma^comp[1]_j> / tr rho for each pair (i, j) in
+ * pairs[np][2] (i != j, Eq. (2Qdef)); connected != 0 subtracts
+ * <sigma_i><sigma_j> (Eq. (etadef)).  out is [B][np] (host or device). */
+int mpdo_measure_2q(mpdo_ctx *ctx, const int *pairs, int np, const char comp[2], int connected,
+                    double *out, int out_on_device);
+
+/* Per-instance status bits (MPDO_ST_*), largest relative discarded weight of
+ * any op since the last build_gates, current bond dimensions chi[B][N-1] and
+ * the trace before the last normalisation trace_before[B].  Any pointer may
+ * be NULL.  Host memory; synchronises the stream. */
+int mpdo_status(mpdo_ctx *ctx, int *status, double *max_discarded, int *chi, double *trace_before);
+
+/* Replace instance b's state: dims[N+1] bond dimensions (dims[0] = dims[N] = 1,
+ * each <= chi_max of b), tensors = the N site tensors (dims[p], 4, dims[p+1])
+ * packed one after another, row-major, host memory.  Schmidt weights are set
+ * to 1.  Used to start from a prepared (e.g. saturated) state. */
+int mpdo_set_state(mpdo_ctx *ctx, int b, const int *dims, const double *tensors);
+
+/* Copy instance b's state out: dims[N+1] and the packed site tensors (at most
+ * cap doubles; returns ECAPACITY if they do not fit).  Host memory. */
+int mpdo_get_state(mpdo_ctx *ctx, int b, int *dims, double *tensors, long long cap);
+
+/* Number of ops (gates + swaps) of one Trotter step, and of swaps. */
+int mpdo_op_counts(mpdo_ctx *ctx, int *n_ops, int *n_swaps, int *n_layers);
+
+/* Rank log: the truncation rank k of every op of the last mpdo_trotter_step
+ * call, [B][n_steps * n_ops] in step order.  cap = capacity of k in ints. */
+int mpdo_rank_log(mpdo_ctx *ctx, int *k, long long cap);
+
+/* Copy instance b's gate matrices out: [n_ops][16][16] row-major doubles in
+ * step order (swaps included), host memory, cap = capacity in doubles. */
+int mpdo_gates(mpdo_ctx *ctx, int b, double *out, long long cap);
+
+/* Host-only (no GPU needed): the op list of one Trotter step for an n-qubit
+ * path with the given bonds.  ops[k*7 + (0..6)] = (layer, kind 0 gate /
+ * 1 swap, left position p, qubit at p, qubit at p+1, bond index or -1,
+ * fraction of dt times 2).  cap = capacity of ops in ints; *n_ops receives
+ * the number of ops (also when ops is NULL).  EINVAL for a bad graph. */
+int mpdo_schedule(int n, int n_bonds, const int *bond_i, const int *bond_j, int *ops, long long cap,
+                  int *n_ops);
+
+/* Kernel timing.  mpdo_profile_enable(ctx, 1) brackets every kernel launch
+ * of the step with CUDA events on the context stream and accumulates, per
+ * kernel kind k (0 merge+gate, 1 Jacobi SVD, 2 truncate, 3 reconstruct,
+ * 4 trace, 5 environments/measure, 6 gate build), the device time in ms,
+ * the number of launches and the algorithmic flops of the work launched
+ * (merge 32 cl cm cr, gate 512 cl cr, SVD 21 n^3 with n = 4 max(cl, cr),
+ * reconstruct 32 cl cr k; 0 for the other kinds).  mpdo_profile_read copies
+ * up to kmax kinds (any pointer may be NULL) and, if reset != 0, zeroes them. */
+int mpdo_profile_enable(mpdo_ctx *ctx, int on);
+int mpdo_profile_read(mpdo_ctx *ctx, double *ms, long long *launches, double *flops, int kmax, int reset);
+
+/* Message of the last error on this thread ("" if none). */
+const char *mpdo_last_error(void);
+
+/* Free every device buffer of the context (NULL is a no-op). */
+void mpdo_destroy(mpdo_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPDO_H */

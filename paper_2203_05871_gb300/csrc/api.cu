@@ -1,0 +1,816 @@
+// C ABI of libmpdo: context, validation, the Trotter-step driver and the
+// measurement entry points (declared and documented in include/mpdo.h).
+#include <mpdo.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace mpdo;
+
+namespace {
+
+thread_local std::string g_err;
+constexpr int kProfKinds = 7;
+enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6 };
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(MPDO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
+    } while (0)
+
+template <class T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void**)p, count * sizeof(T));
+}
+
+// rho(t0) site vectors: v[b][q][4] -> site (b, q), element [0][s][0]
+__global__ void init_product_kernel(double* sites, const double* v, int N, int cap) {
+    const int b = blockIdx.x, q = threadIdx.x;
+    if (q >= N) return;
+    double* S = sites + ((size_t)b * N + q) * (size_t)cap * 4 * cap;
+    for (int s = 0; s < 4; ++s) S[(size_t)s * cap] = v[((size_t)b * N + q) * 4 + s];
+}
+
+}  // namespace
+
+struct mpdo_ctx {
+    mpdo_config cfg{};
+    cudaStream_t st = nullptr;
+    int dev = 0;
+    int N = 0, B = 0, cap = 0, ld = 0;
+    bool built = false;
+    // schedule
+    std::vector<Layer> layers;
+    std::vector<double> weights;
+    std::vector<int> layer_op0;   // op index of each layer's first op
+    int n_ops = 0, n_swaps = 0, max_layer = 0;
+    int nb = 0;
+    std::vector<int> chi_max;
+    std::vector<double> cutoff;
+    // state (device)
+    double* d_sites = nullptr;    // [B][N][cap][4][cap]
+    double* d_lam = nullptr;      // [B][N][cap]   lambda_p for p = 0..N-2
+    int* d_dims = nullptr;        // [B][N+1]
+    int* d_status = nullptr;      // [B]
+    double* d_maxdisc = nullptr;  // [B]
+    double* d_trace = nullptr;    // [B]
+    double* d_params = nullptr;   // [B][6N + 2nb]
+    double* d_gates = nullptr;    // [B][n_ops][256]
+    GateSpec* d_specs = nullptr;
+    // per-slot workspaces
+    int slots = 0;
+    double *d_thetap = nullptr, *d_W = nullptr, *d_Z = nullptr, *d_Yk = nullptr, *d_snorm = nullptr;
+    OpDesc* d_desc = nullptr;
+    OpDesc* h_desc = nullptr;     // pinned
+    int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]
+    unsigned* d_sync = nullptr;
+    int jacobi_resident = 0;
+    // measurement
+    double *d_envL = nullptr, *d_envR = nullptr, *d_full = nullptr, *d_one_a = nullptr, *d_one_b = nullptr,
+           *d_out = nullptr;
+    int *d_q = nullptr, *d_pairs = nullptr;
+    unsigned char* d_need = nullptr;
+    // host mirrors
+    std::vector<int> h_dims;
+    std::vector<int> rank_log;    // [B][steps*n_ops] of the last trotter_step call
+    int rank_steps = 0;
+    // profiling
+    bool prof = false;
+    cudaEvent_t ev[2 * kProfKinds] = {};
+    double prof_ms[kProfKinds] = {};
+    long long prof_launch[kProfKinds] = {};
+    double prof_flops[kProfKinds] = {};
+};
+
+namespace {
+
+void free_all(mpdo_ctx* c) {
+    void* ptrs[] = {c->d_sites, c->d_lam,   c->d_dims,  c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
+                    c->d_gates, c->d_specs, c->d_thetap, c->d_W,     c->d_Z,       c->d_Yk,    c->d_snorm,
+                    c->d_desc,  c->d_cta,   c->d_sync,  c->d_envL,   c->d_envR,    c->d_full,  c->d_one_a,
+                    c->d_one_b, c->d_out,   c->d_q,     c->d_pairs,  c->d_need};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->h_cta) cudaFreeHost(c->h_cta);
+    for (auto& e : c->ev)
+        if (e) cudaEventDestroy(e);
+}
+
+size_t site_elems(const mpdo_ctx* c) { return (size_t)c->cap * 4 * c->cap; }
+double* site(mpdo_ctx* c, int b, int p) { return c->d_sites + ((size_t)b * c->N + p) * site_elems(c); }
+
+int release_slots(mpdo_ctx* c) {
+    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
+    c->d_desc = nullptr;
+    c->d_cta = nullptr;
+    c->d_sync = nullptr;
+    if (c->h_desc) cudaFreeHost(c->h_desc);
+    if (c->h_cta) cudaFreeHost(c->h_cta);
+    c->h_desc = nullptr;
+    c->h_cta = nullptr;
+    c->slots = 0;
+    return MPDO_OK;
+}
+
+int alloc_slots(mpdo_ctx* c, int want) {
+    release_slots(c);
+    const size_t mat = (size_t)c->ld * c->ld;
+    const size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + c->ld) * sizeof(double);
+    size_t free_b = 0, total_b = 0;
+    CU(cudaMemGetInfo(&free_b, &total_b));
+    const size_t budget = free_b / 2;
+    int s = std::max(1, std::min(want, (int)std::min<size_t>(budget / per_slot_bytes, 1 << 20)));
+    if (c->cfg.max_slots > 0) s = std::min(s, c->cfg.max_slots);
+    s = std::min(s, c->jacobi_resident);   // every op of a chunk needs at least one co-resident Jacobi CTA
+    if ((size_t)s * per_slot_bytes > free_b) return fail(MPDO_ENOMEM, "not enough device memory for one op slot");
+    c->slots = s;
+    CU(dalloc(&c->d_thetap, (size_t)s * mat));
+    CU(dalloc(&c->d_W, (size_t)s * mat));
+    CU(dalloc(&c->d_Z, (size_t)s * mat));
+    CU(dalloc(&c->d_Yk, (size_t)s * c->cap * c->ld));
+    CU(dalloc(&c->d_snorm, (size_t)s * c->ld));
+    CU(dalloc(&c->d_desc, (size_t)s));
+    const int gcap = std::max(c->jacobi_resident, s);
+    CU(dalloc(&c->d_cta, (size_t)(2 * gcap + s)));
+    CU(dalloc(&c->d_sync, (size_t)s * jacobi_sync_words_per_op()));
+    CU(cudaMallocHost((void**)&c->h_desc, sizeof(OpDesc) * s));
+    CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * (2 * gcap + s)));
+    return MPDO_OK;
+}
+
+// Bracket a launch with events when profiling; prof_end reads the time after
+// a stream synchronisation (so only call it where the host waits anyway).
+struct ProfScope {
+    mpdo_ctx* c;
+    int k;
+    ProfScope(mpdo_ctx* c_, int k_) : c(c_), k(k_) {
+        if (c->prof) cudaEventRecord(c->ev[2 * k], c->st);
+    }
+    void stop() {
+        if (c->prof) cudaEventRecord(c->ev[2 * k + 1], c->st);
+    }
+};
+
+void prof_collect(mpdo_ctx* c, int k, double flops) {
+    if (!c->prof) return;
+    float ms = 0.0f;
+    if (cudaEventSynchronize(c->ev[2 * k + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess)
+        c->prof_ms[k] += ms;
+    c->prof_launch[k] += 1;
+    c->prof_flops[k] += flops;
+}
+
+int check_status_code(mpdo_ctx* c) {
+    std::vector<int> st(c->B);
+    CU(cudaMemcpyAsync(st.data(), c->d_status, sizeof(int) * c->B, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    int any = 0;
+    for (int v : st) any |= v;
+    if (any & MPDO_ST_TIMEOUT) return fail(MPDO_ETIMEOUT, "a device-side wait timed out");
+    if (any & MPDO_ST_NONFINITE) return fail(MPDO_ENONFINITE, "non-finite values in some instance");
+    if (any & MPDO_ST_NOCONV) return fail(MPDO_ENOCONV, "Jacobi SVD hit its sweep limit in some instance");
+    return MPDO_OK;
+}
+
+// One chunk of (instance, op) work items of a layer.
+struct Item {
+    int b, layer, idx;
+};
+
+int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
+    const int nops = (int)items.size();
+    const int N = c->N, cap = c->cap, ld = c->ld;
+    const size_t mat = (size_t)ld * ld;
+    std::vector<double> work(nops);
+    for (int s = 0; s < nops; ++s) {
+        const Item& it = items[s];
+        const Op& op = c->layers[it.layer][it.idx];
+        const int b = it.b, p = op.p;
+        const int* dm = &c->h_dims[(size_t)b * (N + 1)];
+        OpDesc& d = c->h_desc[s];
+        d.b = b;
+        d.op = c->layer_op0[it.layer] + it.idx;
+        d.cl = dm[p];
+        d.cm = dm[p + 1];
+        d.cr = dm[p + 2];
+        d.m = 4 * d.cl;
+        d.n = 4 * d.cr;
+        d.transposed = d.m > d.n ? 1 : 0;
+        d.c = std::min(d.m, d.n);
+        d.L = std::max(d.m, d.n);
+        d.chi_max = c->chi_max[b];
+        d.cutoff = c->cutoff[b];
+        d.G = c->d_gates + ((size_t)b * c->n_ops + d.op) * 256;
+        d.A = site(c, b, p);
+        d.B = site(c, b, p + 1);
+        d.lam_left = p > 0 ? c->d_lam + ((size_t)b * N + (p - 1)) * cap : nullptr;
+        d.lam_out = c->d_lam + ((size_t)b * N + p) * cap;
+        d.thetap = c->d_thetap + (size_t)s * mat;
+        d.W = c->d_W + (size_t)s * mat;
+        d.Z = c->d_Z + (size_t)s * mat;
+        d.Yk = c->d_Yk + (size_t)s * cap * ld;
+        d.snorm = c->d_snorm + (size_t)s * ld;
+        d.k_out = c->d_dims + (size_t)b * (N + 1) + p + 1;
+        d.status = c->d_status + b;
+        d.max_disc = c->d_maxdisc + b;
+        d.rank_log = nullptr;
+        work[s] = (double)d.c * d.c * (double)d.L;
+    }
+    CU(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
+    double fl_merge = 0.0, fl_svd = 0.0;
+    for (int s = 0; s < nops; ++s) {
+        const OpDesc& d = c->h_desc[s];
+        fl_merge += 32.0 * d.cl * d.cm * d.cr + 512.0 * d.cl * d.cr;
+        const double nn = 4.0 * std::max(d.cl, d.cr);
+        fl_svd += 21.0 * nn * nn * nn;
+    }
+    ProfScope p_merge(c, K_MERGE);
+    CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
+    p_merge.stop();
+
+    // Jacobi: share the co-resident CTAs among the ops in proportion to work
+    const int JW = jacobi_threads() / 32;
+    const int R = c->jacobi_resident;
+    double wsum = 0.0;
+    for (double w : work) wsum += w;
+    std::vector<int> G(nops, 1);
+    int total = 0;
+    for (int s = 0; s < nops; ++s) {
+        const OpDesc& d = c->h_desc[s];
+        const int need = std::max(1, ((d.c + 1) / 2 + JW - 1) / JW);
+        int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
+        g = std::max(1, std::min(need, g));
+        G[s] = g;
+        total += g;
+    }
+    while (total > R) {   // trim the largest groups until everything is co-resident
+        int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
+        if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident Jacobi CTAs");
+        G[arg]--;
+        total--;
+    }
+    int* h_op = c->h_cta;
+    int* h_rank = c->h_cta + total;
+    int* h_group = c->h_cta + 2 * total;
+    int t = 0;
+    for (int s = 0; s < nops; ++s) {
+        h_group[s] = G[s];
+        for (int g = 0; g < G[s]; ++g, ++t) {
+            h_op[t] = s;
+            h_rank[t] = g;
+        }
+    }
+    int* d_op = c->d_cta;
+    int* d_rank = c->d_cta + total;
+    int* d_group = c->d_cta + 2 * total;
+    CU(cudaMemcpyAsync(c->d_cta, c->h_cta, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+    const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
+    ProfScope p_jac(c, K_JACOBI);
+    CU(launch_jacobi(c->d_desc, nops, d_op, d_rank, d_group, c->d_sync, total, c->cfg.jacobi_max_sweeps,
+                     c->cfg.jacobi_tol, timeout_ns, ld, c->st));
+    p_jac.stop();
+    ProfScope p_tr(c, K_TRUNC);
+    CU(launch_truncate(c->d_desc, nops, cap, c->st));
+    p_tr.stop();
+    ProfScope p_rec(c, K_RECON);
+    CU(launch_reconstruct(c->d_desc, nops, cap, c->st));
+    p_rec.stop();
+    // new bond dimensions back to the host (the next chunk's shapes depend on them)
+    CU(cudaMemcpyAsync(c->h_dims.data(), c->d_dims, sizeof(int) * c->h_dims.size(), cudaMemcpyDeviceToHost,
+                       c->st));
+    CU(cudaStreamSynchronize(c->st));
+    double fl_rec = 0.0;
+    for (int s = 0; s < nops; ++s) {
+        const OpDesc& d = c->h_desc[s];
+        fl_rec += 32.0 * d.cl * d.cr * c->h_dims[(size_t)d.b * (N + 1) + c->layers[items[s].layer][items[s].idx].p + 1];
+    }
+    prof_collect(c, K_MERGE, fl_merge);
+    prof_collect(c, K_JACOBI, fl_svd);
+    prof_collect(c, K_TRUNC, 0.0);
+    prof_collect(c, K_RECON, fl_rec);
+    for (int s = 0; s < nops; ++s) {
+        const Item& it = items[s];
+        const Op& op = c->layers[it.layer][it.idx];
+        const int k = c->h_dims[(size_t)it.b * (N + 1) + op.p + 1];
+        const size_t per_b = (size_t)c->rank_steps * c->n_ops;
+        c->rank_log[(size_t)it.b * per_b + (size_t)step * c->n_ops + c->layer_op0[it.layer] + it.idx] = k;
+    }
+    return MPDO_OK;
+}
+
+int validate_model(mpdo_ctx* c, const mpdo_model* m) {
+    const int N = c->N, B = c->B;
+    if (!m) return fail(MPDO_EINVAL, "model is NULL");
+    if (!m->h_x || !m->h_z || !m->g0 || !m->g2 || !m->J || !m->bond_i || !m->bond_j || !m->chi_max || !m->cutoff)
+        return fail(MPDO_EINVAL, "model: a required array is NULL");
+    if (m->n_bonds < 1) return fail(MPDO_EINVAL, "model: n_bonds must be >= 1");
+    for (int b = 0; b < B; ++b) {
+        if (m->chi_max[b] < 1) return fail(MPDO_EINVAL, "model: chi_max must be >= 1");
+        if (m->chi_max[b] > c->cap) return fail(MPDO_ECAPACITY, "model: chi_max exceeds chi_cap");
+        if (!(m->cutoff[b] >= 0.0) || !std::isfinite(m->cutoff[b]))
+            return fail(MPDO_EINVAL, "model: cutoff must be finite and >= 0");
+        for (int q = 0; q < N; ++q) {
+            const size_t i = (size_t)b * N + q;
+            const double g1 = m->g1 ? m->g1[i] : 0.0;
+            if (!(m->g0[i] >= 0.0) || !(m->g2[i] >= 0.0) || !(g1 >= 0.0))
+                return fail(MPDO_EINVAL, "model: rates g0, g1, g2 must be >= 0");
+            const double hy = m->h_y ? m->h_y[i] : 0.0;
+            if (!std::isfinite(m->h_x[i]) || !std::isfinite(hy) || !std::isfinite(m->h_z[i]) ||
+                !std::isfinite(m->g0[i]) || !std::isfinite(m->g2[i]) || !std::isfinite(g1))
+                return fail(MPDO_EINVAL, "model: non-finite on-site parameter");
+        }
+        for (int k = 0; k < m->n_bonds; ++k) {
+            const size_t i = (size_t)b * m->n_bonds + k;
+            if (!std::isfinite(m->J[i]) || (m->Jz && !std::isfinite(m->Jz[i])))
+                return fail(MPDO_EINVAL, "model: non-finite coupling");
+        }
+    }
+    if (m->init_pauli) {
+        if (strlen(m->init_pauli) != (size_t)(2 * N))
+            return fail(MPDO_EINVAL, "model: init_pauli must have 2N characters");
+        for (int q = 0; q < N; ++q) {
+            const char s = m->init_pauli[2 * q], a = m->init_pauli[2 * q + 1];
+            if ((s != '+' && s != '-') || !strchr("xyzXYZ", a))
+                return fail(MPDO_EINVAL, "model: init_pauli entries must be +x,-x,+y,-y,+z,-z");
+        }
+    }
+    return MPDO_OK;
+}
+
+int pauli_comp(char ch) {
+    switch (ch) {
+        case 'I': case 'i': return 0;
+        case 'X': case 'x': return 1;
+        case 'Y': case 'y': return 2;
+        case 'Z': case 'z': return 3;
+        default: return -1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mpdo_last_error(void) { return g_err.c_str(); }
+
+int mpdo_config_default(mpdo_config* cfg) {
+    if (!cfg) return fail(MPDO_EINVAL, "cfg is NULL");
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->batch = 1;
+    cfg->precision = MPDO_FP64;
+    cfg->storage = MPDO_STORE_F64;
+    cfg->trotter_order = 2;
+    cfg->force_trace = 1;
+    cfg->jacobi_max_sweeps = 40;
+    cfg->jacobi_tol = 0.0;
+    cfg->barrier_timeout_ms = 4000;
+    cfg->max_slots = 0;
+    cfg->device = -1;
+    return MPDO_OK;
+}
+
+int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
+    if (!out || !cfg) return fail(MPDO_EINVAL, "out and cfg must not be NULL");
+    *out = nullptr;
+    if (cfg->n_qubits < 3) return fail(MPDO_EINVAL, "n_qubits must be >= 3");
+    if (cfg->batch < 1) return fail(MPDO_EINVAL, "batch must be >= 1");
+    if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
+    if (cfg->precision != MPDO_FP64) return fail(MPDO_EINVAL, "precision: only MPDO_FP64 is available in this build");
+    if (cfg->storage != MPDO_STORE_F64) return fail(MPDO_EINVAL, "storage: only MPDO_STORE_F64 is available");
+    if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
+    if (cfg->jacobi_max_sweeps < 1 || cfg->jacobi_max_sweeps > kMaxSweepsCap)
+        return fail(MPDO_EINVAL, "jacobi_max_sweeps must be in [1, 128]");
+    if (cfg->barrier_timeout_ms < 1) return fail(MPDO_EINVAL, "barrier_timeout_ms must be >= 1");
+    int dev = cfg->device;
+    if (dev < 0) CU(cudaGetDevice(&dev));
+    CU(cudaSetDevice(dev));
+    mpdo_ctx* c = new (std::nothrow) mpdo_ctx();
+    if (!c) return fail(MPDO_ENOMEM, "host allocation failed");
+    c->dev = dev;
+    c->cfg = *cfg;
+    c->st = (cudaStream_t)cuda_stream;
+    c->N = cfg->n_qubits;
+    c->B = cfg->batch;
+    c->cap = cfg->chi_cap;
+    c->ld = 4 * cfg->chi_cap;
+    const int N = c->N, B = c->B;
+    auto bail = [&](int code) {
+        free_all(c);
+        delete c;
+        return code;
+    };
+    cudaError_t e;
+    if ((e = dalloc(&c->d_sites, (size_t)B * N * site_elems(c))) != cudaSuccess ||
+        (e = dalloc(&c->d_lam, (size_t)B * N * c->cap)) != cudaSuccess ||
+        (e = dalloc(&c->d_dims, (size_t)B * (N + 1))) != cudaSuccess ||
+        (e = dalloc(&c->d_status, (size_t)B)) != cudaSuccess ||
+        (e = dalloc(&c->d_maxdisc, (size_t)B)) != cudaSuccess ||
+        (e = dalloc(&c->d_trace, (size_t)B)) != cudaSuccess ||
+        (e = dalloc(&c->d_envL, (size_t)B * (N + 1) * c->cap)) != cudaSuccess ||
+        (e = dalloc(&c->d_envR, (size_t)B * (N + 1) * c->cap)) != cudaSuccess ||
+        (e = dalloc(&c->d_full, (size_t)B * N * N)) != cudaSuccess ||
+        (e = dalloc(&c->d_one_a, (size_t)B * N * 4)) != cudaSuccess ||
+        (e = dalloc(&c->d_one_b, (size_t)B * N)) != cudaSuccess ||
+        (e = dalloc(&c->d_out, (size_t)B * N * N)) != cudaSuccess ||
+        (e = dalloc(&c->d_q, (size_t)N)) != cudaSuccess ||
+        (e = dalloc(&c->d_pairs, (size_t)3 * N * N)) != cudaSuccess ||
+        (e = dalloc(&c->d_need, (size_t)N)) != cudaSuccess) {
+        fail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA,
+             std::string("device allocation: ") + cudaGetErrorString(e));
+        return bail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA);
+    }
+    if ((e = jacobi_max_resident(&c->jacobi_resident)) != cudaSuccess || c->jacobi_resident < 1) {
+        fail(MPDO_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+        return bail(MPDO_ECUDA);
+    }
+    for (auto& ev : c->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+            fail(MPDO_ECUDA, std::string("event create: ") + cudaGetErrorString(e));
+            return bail(MPDO_ECUDA);
+        }
+    c->h_dims.assign((size_t)B * (N + 1), 1);
+    *out = c;
+    return MPDO_OK;
+}
+
+int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    CU(cudaSetDevice(c->dev));
+    if (!std::isfinite(dt)) return fail(MPDO_EINVAL, "dt must be finite");
+    int rc = validate_model(c, m);
+    if (rc) return rc;
+    const int N = c->N, B = c->B, nb = m->n_bonds;
+    std::vector<int> bi(m->bond_i, m->bond_i + nb), bj(m->bond_j, m->bond_j + nb);
+    std::vector<Layer> layers;
+    std::vector<double> weights;
+    std::string err = build_schedule(N, bi, bj, layers, weights);
+    if (!err.empty()) return fail(MPDO_EINVAL, "bond graph: " + err);
+    c->layers = layers;
+    c->weights = weights;
+    c->nb = nb;
+    c->layer_op0.clear();
+    c->n_ops = c->n_swaps = c->max_layer = 0;
+    for (auto& L : layers) {
+        c->layer_op0.push_back(c->n_ops);
+        c->n_ops += (int)L.size();
+        c->max_layer = std::max(c->max_layer, (int)L.size());
+        for (auto& o : L) c->n_swaps += o.kind;
+    }
+    c->chi_max.assign(m->chi_max, m->chi_max + B);
+    c->cutoff.assign(m->cutoff, m->cutoff + B);
+    // parameters
+    const int P = 6 * N + 2 * nb;
+    std::vector<double> hp((size_t)B * P, 0.0);
+    for (int b = 0; b < B; ++b) {
+        double* dst = &hp[(size_t)b * P];
+        for (int q = 0; q < N; ++q) {
+            const size_t i = (size_t)b * N + q;
+            dst[0 * N + q] = m->h_x[i];
+            dst[1 * N + q] = m->h_y ? m->h_y[i] : 0.0;
+            dst[2 * N + q] = m->h_z[i];
+            dst[3 * N + q] = m->g0[i];
+            dst[4 * N + q] = m->g1 ? m->g1[i] : 0.0;
+            dst[5 * N + q] = m->g2[i];
+        }
+        for (int k = 0; k < nb; ++k) {
+            dst[6 * N + k] = m->J[(size_t)b * nb + k];
+            dst[6 * N + nb + k] = m->Jz ? m->Jz[(size_t)b * nb + k] : 0.0;
+        }
+    }
+    std::vector<GateSpec> specs;
+    specs.reserve((size_t)B * c->n_ops);
+    for (int b = 0; b < B; ++b)
+        for (auto& L : layers)
+            for (auto& o : L)
+                specs.push_back(GateSpec{b, o.kind, o.qa, o.qb, o.bond, o.frac * dt, weights[o.qa], weights[o.qb]});
+    // (re)allocate graph-sized buffers
+    if (c->d_params) cudaFree(c->d_params);
+    if (c->d_gates) cudaFree(c->d_gates);
+    if (c->d_specs) cudaFree(c->d_specs);
+    c->d_params = nullptr;
+    c->d_gates = nullptr;
+    c->d_specs = nullptr;
+    CU(dalloc(&c->d_params, hp.size()));
+    CU(dalloc(&c->d_gates, (size_t)B * c->n_ops * 256));
+    CU(dalloc(&c->d_specs, specs.size()));
+    CU(cudaMemcpyAsync(c->d_params, hp.data(), sizeof(double) * hp.size(), cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemcpyAsync(c->d_specs, specs.data(), sizeof(GateSpec) * specs.size(), cudaMemcpyHostToDevice, c->st));
+    CU(launch_build_gates(c->d_specs, (int)specs.size(), N, nb, c->d_params, c->d_gates, c->st));
+    const int want = B * c->max_layer;
+    if (c->slots < want) {
+        rc = alloc_slots(c, want);
+        if (rc) return rc;
+    }
+    // initial product state (Sec. 2.2): site vector (1, +-1 at a)/sqrt2, chi = 1
+    const double r2 = 1.0 / std::sqrt(2.0);
+    std::vector<double> v0((size_t)B * N * 4, 0.0);
+    for (int b = 0; b < B; ++b)
+        for (int q = 0; q < N; ++q) {
+            double* v = &v0[((size_t)b * N + q) * 4];
+            v[0] = r2;
+            if (m->init_pauli) {
+                const double sg = m->init_pauli[2 * q] == '+' ? 1.0 : -1.0;
+                v[pauli_comp(m->init_pauli[2 * q + 1])] += sg * r2;
+            } else {
+                v[3] += r2;
+            }
+        }
+    CU(cudaMemsetAsync(c->d_sites, 0, sizeof(double) * (size_t)B * N * site_elems(c), c->st));
+    CU(cudaMemcpyAsync(c->d_one_a, v0.data(), sizeof(double) * v0.size(), cudaMemcpyHostToDevice, c->st));
+    init_product_kernel<<<B, 64, 0, c->st>>>(c->d_sites, c->d_one_a, N, c->cap);
+    CU(cudaGetLastError());
+    std::vector<double> ones((size_t)B * N * c->cap, 1.0);
+    CU(cudaMemcpyAsync(c->d_lam, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, c->st));
+    c->h_dims.assign((size_t)B * (N + 1), 1);
+    CU(cudaMemcpyAsync(c->d_dims, c->h_dims.data(), sizeof(int) * c->h_dims.size(), cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemsetAsync(c->d_status, 0, sizeof(int) * B, c->st));
+    CU(cudaMemsetAsync(c->d_maxdisc, 0, sizeof(double) * B, c->st));
+    CU(cudaMemsetAsync(c->d_trace, 0, sizeof(double) * B, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    c->built = true;
+    return MPDO_OK;
+}
+
+int mpdo_trotter_step(mpdo_ctx* c, int n_steps) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    if (n_steps < 0) return fail(MPDO_EINVAL, "n_steps must be >= 0");
+    c->rank_steps = n_steps;
+    c->rank_log.assign((size_t)c->B * n_steps * c->n_ops, 0);
+    for (int step = 0; step < n_steps; ++step) {
+        for (int li = 0; li < (int)c->layers.size(); ++li) {
+            std::vector<Item> items;
+            for (int b = 0; b < c->B; ++b)
+                for (int i = 0; i < (int)c->layers[li].size(); ++i) items.push_back(Item{b, li, i});
+            for (size_t s0 = 0; s0 < items.size(); s0 += c->slots) {
+                std::vector<Item> chunk(items.begin() + s0,
+                                        items.begin() + std::min(items.size(), s0 + (size_t)c->slots));
+                int rc = run_chunk(c, chunk, step);
+                if (rc) return rc;
+            }
+        }
+        ProfScope p_trace(c, K_TRACE);
+        CU(launch_trace_normalize(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
+                                  c->d_status, c->st));
+        p_trace.stop();
+        prof_collect(c, K_TRACE, 0.0);
+    }
+    return check_status_code(c);
+}
+
+int mpdo_measure_1q(mpdo_ctx* c, const int* qubits, int nq, char comp, double* out, int out_on_device) {
+    if (!c || !qubits || !out) return fail(MPDO_EINVAL, "NULL argument");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    const int a = pauli_comp(comp);
+    if (a < 0) return fail(MPDO_EINVAL, "comp must be one of I, X, Y, Z");
+    if (nq < 0 || nq > c->N) return fail(MPDO_EINVAL, "nq must be in [0, N]");
+    for (int k = 0; k < nq; ++k)
+        if (qubits[k] < 0 || qubits[k] >= c->N) return fail(MPDO_EINVAL, "qubit index out of range");
+    if (nq == 0) return MPDO_OK;
+    CU(cudaMemcpyAsync(c->d_q, qubits, sizeof(int) * nq, cudaMemcpyHostToDevice, c->st));
+    CU(launch_environments(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->st));
+    double* dst = out_on_device ? out : c->d_out;
+    CU(launch_measure_1q(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->d_q, nq, a, dst, c->st));
+    if (!out_on_device) {
+        CU(cudaMemcpyAsync(out, c->d_out, sizeof(double) * nq * c->B, cudaMemcpyDeviceToHost, c->st));
+        CU(cudaStreamSynchronize(c->st));
+    }
+    return MPDO_OK;
+}
+
+int mpdo_measure_2q(mpdo_ctx* c, const int* pairs, int np, const char comp[2], int connected, double* out,
+                    int out_on_device) {
+    if (!c || !pairs || !out || !comp) return fail(MPDO_EINVAL, "NULL argument");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    const int ca = pauli_comp(comp[0]), cb = pauli_comp(comp[1]);
+    if (ca < 0 || cb < 0) return fail(MPDO_EINVAL, "comp entries must be I, X, Y, Z");
+    const int N = c->N, B = c->B;
+    if (np < 0 || np > N * N) return fail(MPDO_ECAPACITY, "np must be in [0, N*N]");
+    if (np == 0) return MPDO_OK;
+    for (int k = 0; k < np; ++k) {
+        const int i = pairs[2 * k], j = pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= N || j >= N || i == j) return fail(MPDO_EINVAL, "pair indices out of range or i == j");
+    }
+    CU(launch_environments(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->st));
+    std::vector<int> allq(N);
+    for (int q = 0; q < N; ++q) allq[q] = q;
+    CU(cudaMemcpyAsync(c->d_q, allq.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
+    CU(launch_measure_1q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, ca, c->d_one_a, c->st));
+    CU(launch_measure_1q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, cb, c->d_one_b, c->st));
+    double* dst = out_on_device ? out : c->d_out;
+    for (int pass = 0; pass < 2; ++pass) {
+        // pass 0: pairs with i < j; pass 1: pairs with i > j, evaluated as (j, i) with swapped components
+        std::vector<int> trip;
+        std::vector<unsigned char> need(N, 0);
+        for (int k = 0; k < np; ++k) {
+            int i = pairs[2 * k], j = pairs[2 * k + 1];
+            if ((pass == 0) != (i < j)) continue;
+            if (pass == 1) std::swap(i, j);
+            trip.push_back(i);
+            trip.push_back(j);
+            trip.push_back(k);
+            need[i] = 1;
+        }
+        if (trip.empty()) continue;
+        const int x = pass == 0 ? ca : cb, y = pass == 0 ? cb : ca;
+        CU(cudaMemcpyAsync(c->d_need, need.data(), N, cudaMemcpyHostToDevice, c->st));
+        CU(launch_measure_2q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, x, y, c->d_need, c->d_full,
+                             c->st));
+        CU(cudaMemcpyAsync(c->d_pairs, trip.data(), sizeof(int) * trip.size(), cudaMemcpyHostToDevice, c->st));
+        const double* oa = pass == 0 ? c->d_one_a : c->d_one_b;
+        const double* ob = pass == 0 ? c->d_one_b : c->d_one_a;
+        CU(launch_gather_2q(c->d_full, oa, ob, c->d_pairs, (int)trip.size() / 3, np, N, B, connected, dst, c->st));
+        CU(cudaStreamSynchronize(c->st));   // host vectors above are reused by the next pass
+    }
+    if (!out_on_device) {
+        CU(cudaMemcpyAsync(out, dst, sizeof(double) * (size_t)np * B, cudaMemcpyDeviceToHost, c->st));
+        CU(cudaStreamSynchronize(c->st));
+    }
+    return MPDO_OK;
+}
+
+int mpdo_status(mpdo_ctx* c, int* status, double* max_discarded, int* chi, double* trace_before) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    CU(cudaSetDevice(c->dev));
+    const int B = c->B, N = c->N;
+    if (status) CU(cudaMemcpyAsync(status, c->d_status, sizeof(int) * B, cudaMemcpyDeviceToHost, c->st));
+    if (max_discarded) CU(cudaMemcpyAsync(max_discarded, c->d_maxdisc, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st));
+    if (trace_before) CU(cudaMemcpyAsync(trace_before, c->d_trace, sizeof(double) * B, cudaMemcpyDeviceToHost, c->st));
+    CU(cudaMemcpyAsync(c->h_dims.data(), c->d_dims, sizeof(int) * c->h_dims.size(), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    if (chi)
+        for (int b = 0; b < B; ++b)
+            for (int p = 0; p < N - 1; ++p) chi[(size_t)b * (N - 1) + p] = c->h_dims[(size_t)b * (N + 1) + p + 1];
+    return MPDO_OK;
+}
+
+int mpdo_set_state(mpdo_ctx* c, int b, const int* dims, const double* tensors) {
+    if (!c || !dims || !tensors) return fail(MPDO_EINVAL, "NULL argument");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    const int N = c->N;
+    if (b < 0 || b >= c->B) return fail(MPDO_EINVAL, "instance out of range");
+    if (dims[0] != 1 || dims[N] != 1) return fail(MPDO_EINVAL, "dims[0] and dims[N] must be 1");
+    for (int p = 1; p < N; ++p)
+        if (dims[p] < 1 || dims[p] > c->chi_max[b]) return fail(MPDO_ECAPACITY, "bond dimension out of [1, chi_max]");
+    size_t off = 0;
+    std::vector<double> buf((size_t)c->cap * 4 * c->cap);
+    for (int p = 0; p < N; ++p) {
+        const int cl = dims[p], cr = dims[p + 1];
+        std::fill(buf.begin(), buf.end(), 0.0);
+        for (int l = 0; l < cl; ++l)
+            for (int s = 0; s < 4; ++s)
+                for (int r = 0; r < cr; ++r) buf[((size_t)l * 4 + s) * c->cap + r] = tensors[off + ((size_t)l * 4 + s) * cr + r];
+        off += (size_t)cl * 4 * cr;
+        CU(cudaMemcpyAsync(site(c, b, p), buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->st));
+        CU(cudaStreamSynchronize(c->st));
+    }
+    std::vector<double> ones((size_t)N * c->cap, 1.0);
+    CU(cudaMemcpyAsync(c->d_lam + (size_t)b * N * c->cap, ones.data(), sizeof(double) * ones.size(),
+                       cudaMemcpyHostToDevice, c->st));
+    for (int p = 0; p <= N; ++p) c->h_dims[(size_t)b * (N + 1) + p] = dims[p];
+    CU(cudaMemcpyAsync(c->d_dims, c->h_dims.data(), sizeof(int) * c->h_dims.size(), cudaMemcpyHostToDevice, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return MPDO_OK;
+}
+
+int mpdo_get_state(mpdo_ctx* c, int b, int* dims, double* tensors, long long cap_elems) {
+    if (!c || !dims) return fail(MPDO_EINVAL, "NULL argument");
+    CU(cudaSetDevice(c->dev));
+    if (b < 0 || b >= c->B) return fail(MPDO_EINVAL, "instance out of range");
+    const int N = c->N;
+    CU(cudaMemcpyAsync(c->h_dims.data(), c->d_dims, sizeof(int) * c->h_dims.size(), cudaMemcpyDeviceToHost, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    long long need = 0;
+    for (int p = 0; p <= N; ++p) dims[p] = c->h_dims[(size_t)b * (N + 1) + p];
+    for (int p = 0; p < N; ++p) need += (long long)dims[p] * 4 * dims[p + 1];
+    if (!tensors) return MPDO_OK;
+    if (need > cap_elems) return fail(MPDO_ECAPACITY, "tensor buffer too small");
+    std::vector<double> buf((size_t)c->cap * 4 * c->cap);
+    size_t off = 0;
+    for (int p = 0; p < N; ++p) {
+        CU(cudaMemcpyAsync(buf.data(), site(c, b, p), sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, c->st));
+        CU(cudaStreamSynchronize(c->st));
+        const int cl = dims[p], cr = dims[p + 1];
+        for (int l = 0; l < cl; ++l)
+            for (int s = 0; s < 4; ++s)
+                for (int r = 0; r < cr; ++r) tensors[off + ((size_t)l * 4 + s) * cr + r] = buf[((size_t)l * 4 + s) * c->cap + r];
+        off += (size_t)cl * 4 * cr;
+    }
+    return MPDO_OK;
+}
+
+int mpdo_op_counts(mpdo_ctx* c, int* n_ops, int* n_swaps, int* n_layers) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    if (n_ops) *n_ops = c->n_ops;
+    if (n_swaps) *n_swaps = c->n_swaps;
+    if (n_layers) *n_layers = (int)c->layers.size();
+    return MPDO_OK;
+}
+
+int mpdo_rank_log(mpdo_ctx* c, int* k, long long cap) {
+    if (!c || !k) return fail(MPDO_EINVAL, "NULL argument");
+    if ((long long)c->rank_log.size() > cap) return fail(MPDO_ECAPACITY, "rank log buffer too small");
+    std::copy(c->rank_log.begin(), c->rank_log.end(), k);
+    return MPDO_OK;
+}
+
+int mpdo_gates(mpdo_ctx* c, int b, double* out, long long cap) {
+    if (!c || !out) return fail(MPDO_EINVAL, "NULL argument");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    if (b < 0 || b >= c->B) return fail(MPDO_EINVAL, "instance out of range");
+    const long long need = (long long)c->n_ops * 256;
+    if (need > cap) return fail(MPDO_ECAPACITY, "gate buffer too small");
+    CU(cudaMemcpyAsync(out, c->d_gates + (size_t)b * c->n_ops * 256, sizeof(double) * need, cudaMemcpyDeviceToHost,
+                       c->st));
+    CU(cudaStreamSynchronize(c->st));
+    return MPDO_OK;
+}
+
+int mpdo_schedule(int n, int n_bonds, const int* bond_i, const int* bond_j, int* ops, long long cap, int* n_ops) {
+    if (!bond_i || !bond_j || !n_ops) return fail(MPDO_EINVAL, "NULL argument");
+    if (n < 2 || n_bonds < 1) return fail(MPDO_EINVAL, "need n >= 2 and n_bonds >= 1");
+    std::vector<int> bi(bond_i, bond_i + n_bonds), bj(bond_j, bond_j + n_bonds);
+    std::vector<Layer> layers;
+    std::vector<double> w;
+    std::string err = build_schedule(n, bi, bj, layers, w);
+    if (!err.empty()) return fail(MPDO_EINVAL, "bond graph: " + err);
+    long long k = 0;
+    for (size_t li = 0; li < layers.size(); ++li)
+        for (const Op& o : layers[li]) {
+            if (ops) {
+                if ((k + 1) * 7 > cap) return fail(MPDO_ECAPACITY, "ops buffer too small");
+                int* r = ops + k * 7;
+                r[0] = (int)li;
+                r[1] = o.kind;
+                r[2] = o.p;
+                r[3] = o.qa;
+                r[4] = o.qb;
+                r[5] = o.bond;
+                r[6] = (int)std::lround(o.frac * 2.0);
+            }
+            ++k;
+        }
+    *n_ops = (int)k;
+    return MPDO_OK;
+}
+
+int mpdo_profile_enable(mpdo_ctx* c, int on) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    c->prof = on != 0;
+    return MPDO_OK;
+}
+
+int mpdo_profile_read(mpdo_ctx* c, double* ms, long long* launches, double* flops, int kmax, int reset) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    for (int k = 0; k < std::min(kmax, kProfKinds); ++k) {
+        if (ms) ms[k] = c->prof_ms[k];
+        if (launches) launches[k] = c->prof_launch[k];
+        if (flops) flops[k] = c->prof_flops[k];
+    }
+    if (reset)
+        for (int k = 0; k < kProfKinds; ++k) {
+            c->prof_ms[k] = 0.0;
+            c->prof_launch[k] = 0;
+            c->prof_flops[k] = 0.0;
+        }
+    return MPDO_OK;
+}
+
+void mpdo_destroy(mpdo_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->st) cudaStreamSynchronize(c->st);
+    else cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal declarations shared by the libmpdo translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace mpdo {
+
+constexpr int kMaxChi = 512;          // chi_cap upper bound (config: N=40 grid at chi=512)
+constexpr int kMaxSweepsCap = 128;    // size of the per-op rotation-counter array
+
+// ---------------------------------------------------------------------------
+// Trotter schedule (host).  One op acts on path positions (p, p+1).
+// ---------------------------------------------------------------------------
+struct Op {
+    int kind;      // 0 = gate, 1 = swap
+    int p;         // left path position
+    int qa, qb;    // qubits at p and p+1 before the op
+    int bond;      // bond index (gates), -1 for swaps
+    double frac;   // fraction of dt (gates), 0 for swaps
+};
+using Layer = std::vector<Op>;
+
+// Builds the layers of one second-order step; returns "" or an error message.
+std::string build_schedule(int n, const std::vector<int>& bi, const std::vector<int>& bj,
+                           std::vector<Layer>& layers, std::vector<double>& weights);
+
+// ---------------------------------------------------------------------------
+// Per-op descriptor of one two-site update, filled by the host per layer.
+// All pointers are device pointers.  Matrices in the workspace are row-major
+// with leading dimension ld = 4 * chi_cap.
+// ---------------------------------------------------------------------------
+struct OpDesc {
+    int b;             // instance
+    int op;            // op index within the step (for the rank log)
+    int cl, cm, cr;    // bond dims chi_{p-1}, chi_p, chi_{p+1}
+    int m, n;          // 4*cl, 4*cr
+    int transposed;    // 1: Jacobi rows are the columns of theta~ (m > n), with Z
+    int c, L;          // Jacobi problem: c rows of length L
+    int chi_max;
+    double cutoff;
+    const double* G;   // 16x16 gate, row-major G[(s1' s2'), (s1 s2)]
+    double* A;         // site p    [cl][4][chi_cap]
+    double* B;         // site p+1  [cm][4][chi_cap]
+    const double* lam_left;  // lambda_{p-1} (nullptr => 1)
+    double* lam_out;   // lambda_p
+    double* thetap;    // Theta'  m x n (ld)
+    double* W;         // Jacobi rows: theta~ (m x n) or theta~^T (n x m)
+    double* Z;         // c x c rotation accumulator when transposed
+    double* Yk;        // k x n right singular vectors (rows), ld
+    double* snorm;     // c row norms (scratch)
+    int* k_out;        // new chi_p
+    int* status;       // per-instance status word
+    double* max_disc;  // per-instance max discarded weight
+    int* rank_log;     // &log[b][step*n_ops + op] or nullptr
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (each returns the cudaError_t of the launch)
+// ---------------------------------------------------------------------------
+struct GateSpec {        // one gate to build
+    int b;               // instance
+    int kind;            // 0 gate, 1 swap
+    int qa, qb, bond;
+    double tau;          // frac * dt
+    double wa, wb;       // on-site weights 1/deg
+};
+cudaError_t launch_build_gates(const GateSpec* d_specs, int count, int n, int nb,
+                               const double* d_params, double* d_gates, cudaStream_t st);
+
+cudaError_t launch_merge_gate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+cudaError_t launch_reconstruct(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+
+struct JacobiPlan {
+    int grid;            // total CTAs (cooperative)
+    int max_resident;    // co-resident capacity
+};
+int jacobi_threads();
+cudaError_t jacobi_max_resident(int* blocks);
+// d_cta_op[grid]: op index of each CTA; d_cta_rank[grid]: rank within its op;
+// d_group[nops]: CTAs per op.  d_sync: per-op counters (zeroed by the caller,
+// layout documented in jacobi.cu).
+cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
+                          const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
+                          unsigned long long timeout_ns, int ld, cudaStream_t st);
+size_t jacobi_sync_words_per_op();
+
+cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+
+cudaError_t launch_trace_normalize(double* sites, const int* dims, int n, int B, int chi_cap,
+                                   int force, double* trace_out, int* status, cudaStream_t st);
+cudaError_t launch_environments(const double* sites, const int* dims, int n, int B, int chi_cap,
+                                double* envL, double* envR, cudaStream_t st);
+// E(comp at q) for the listed qubits: out[b][k] = <sigma^c_q> (divided by E0)
+cudaError_t launch_measure_1q(const double* sites, const int* dims, int n, int B, int chi_cap,
+                              const double* envL, const double* envR, const int* d_q, int nq,
+                              int comp, double* out, cudaStream_t st);
+// all-pairs propagation: for each (b, i) computes E(ca at i, cb at j) for j > i
+// into full[b][i][j]; unused entries untouched.
+cudaError_t launch_measure_2q(const double* sites, const int* dims, int n, int B, int chi_cap,
+                              const double* envL, const double* envR, int ca, int cb,
+                              const unsigned char* d_need_i, double* full, cudaStream_t st);
+// d_trip[m][3] = (i, j, k): out[b][k] = full[b][i][j] (- one_a[b][i] one_b[b][j] if connected)
+cudaError_t launch_gather_2q(const double* full, const double* one_a, const double* one_b,
+                             const int* d_trip, int m, int np, int n, int B, int connected,
+                             double* out, cudaStream_t st);
+
+}  // namespace mpdo

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libmpdo (include/mpdo.h): argument marshalling only.
+
+Every step of the solver runs in the library's CUDA kernels; this module only
+converts numpy / torch arguments to pointers.  If the shared library is
+missing it raises immediately: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmpdo.so")
+
+MPDO_OK, MPDO_EINVAL, MPDO_ENOMEM, MPDO_ECUDA, MPDO_ENOCONV, MPDO_ETIMEOUT, MPDO_ENONFINITE, \
+    MPDO_ECAPACITY, MPDO_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
+ST_NOCONV, ST_NONFINITE, ST_TIMEOUT, ST_CAPACITY = 1, 2, 4, 8
+FP64, MIXED_TF32, MIXED_BF16X3 = 0, 1, 2
+STORE_F64, STORE_F32 = 0, 1
+
+_ERR_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT",
+              -6: "ENONFINITE", -7: "ECAPACITY", -8: "ESTATE"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("batch", ctypes.c_int), ("chi_cap", ctypes.c_int),
+                ("precision", ctypes.c_int), ("storage", ctypes.c_int), ("trotter_order", ctypes.c_int),
+                ("force_trace", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int),
+                ("jacobi_tol", ctypes.c_double), ("barrier_timeout_ms", ctypes.c_uint),
+                ("max_slots", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class Model(ctypes.Structure):
+    _fields_ = [("h_x", _dp), ("h_y", _dp), ("h_z", _dp), ("g0", _dp), ("g1", _dp), ("g2", _dp),
+                ("n_bonds", ctypes.c_int), ("bond_i", _ip), ("bond_j", _ip), ("J", _dp), ("Jz", _dp),
+                ("chi_max", _ip), ("cutoff", _dp), ("init_pauli", ctypes.c_char_p)]
+
+
+class MpdoError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libmpdo {_ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmpdo.so (built by paper_2203_05871_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libmpdo is not built ({path} missing); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    sig = {
+        "mpdo_config_default": (ctypes.c_int, [ctypes.POINTER(Config)]),
+        "mpdo_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(Config), vp]),
+        "mpdo_build_gates": (ctypes.c_int, [vp, ctypes.POINTER(Model), ctypes.c_double]),
+        "mpdo_trotter_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mpdo_measure_1q": (ctypes.c_int, [vp, _ip, ctypes.c_int, ctypes.c_char, vp, ctypes.c_int]),
+        "mpdo_measure_2q": (ctypes.c_int, [vp, _ip, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, vp,
+                                           ctypes.c_int]),
+        "mpdo_status": (ctypes.c_int, [vp, _ip, _dp, _ip, _dp]),
+        "mpdo_set_state": (ctypes.c_int, [vp, ctypes.c_int, _ip, _dp]),
+        "mpdo_get_state": (ctypes.c_int, [vp, ctypes.c_int, _ip, _dp, ctypes.c_longlong]),
+        "mpdo_op_counts": (ctypes.c_int, [vp, _ip, _ip, _ip]),
+        "mpdo_rank_log": (ctypes.c_int, [vp, _ip, ctypes.c_longlong]),
+        "mpdo_gates": (ctypes.c_int, [vp, ctypes.c_int, _dp, ctypes.c_longlong]),
+        "mpdo_schedule": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _ip, _ip, _ip, ctypes.c_longlong, _ip]),
+        "mpdo_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mpdo_profile_read": (ctypes.c_int, [vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, ctypes.c_int,
+                                             ctypes.c_int]),
+        "mpdo_last_error": (ctypes.c_char_p, []),
+        "mpdo_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    """Names declared in include/mpdo.h (for the export test)."""
+    return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_measure_1q",
+            "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
+            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read",
+            "mpdo_last_error", "mpdo_destroy"]
+
+
+PROFILE_KINDS = ["merge_gate", "jacobi_svd", "truncate", "reconstruct", "trace", "measure", "build_gates"]
+
+
+def schedule(n: int, bonds):
+    """Host-only op list of one Trotter step: list of layers of
+    (kind, p, qa, qb, bond, frac) tuples, as computed by libmpdo."""
+    lib = load_library()
+    bi = _as([b[0] for b in bonds], np.int32)
+    bj = _as([b[1] for b in bonds], np.int32)
+    cnt = ctypes.c_int()
+    _check(lib.mpdo_schedule(n, len(bonds), _ptr(bi, ctypes.c_int), _ptr(bj, ctypes.c_int), None, 0,
+                             ctypes.byref(cnt)))
+    buf = np.zeros(cnt.value * 7, np.int32)
+    _check(lib.mpdo_schedule(n, len(bonds), _ptr(bi, ctypes.c_int), _ptr(bj, ctypes.c_int),
+                             _ptr(buf, ctypes.c_int), len(buf), ctypes.byref(cnt)))
+    layers = []
+    for r in buf.reshape(-1, 7):
+        li, kind, p, qa, qb, bond, f2 = (int(x) for x in r)
+        while len(layers) <= li:
+            layers.append([])
+        layers[li].append(("swap" if kind else "gate", p, qa, qb, bond, f2 / 2.0))
+    return layers
+
+
+def _check(code):
+    if code != MPDO_OK:
+        raise MpdoError(code, _lib.mpdo_last_error().decode())
+    return code
+
+
+def _as(arr, dtype):
+    return np.ascontiguousarray(np.asarray(arr, dtype=dtype))
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+class Solver:
+    """One libmpdo context: B instances of an N-qubit model on one GPU."""
+
+    def __init__(self, n_qubits: int, batch: int = 1, chi_cap: int = 32, precision: int = FP64,
+                 storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 40,
+                 jacobi_tol: float = 0.0, barrier_timeout_ms: int = 4000, max_slots: int = 0,
+                 device: Optional[int] = None):
+        lib = load_library()
+        cfg = Config()
+        _check(lib.mpdo_config_default(ctypes.byref(cfg)))
+        cfg.n_qubits, cfg.batch, cfg.chi_cap = n_qubits, batch, chi_cap
+        cfg.precision, cfg.storage = precision, storage
+        cfg.force_trace = 1 if force_trace else 0
+        cfg.jacobi_max_sweeps, cfg.jacobi_tol = jacobi_max_sweeps, jacobi_tol
+        cfg.barrier_timeout_ms, cfg.max_slots = barrier_timeout_ms, max_slots
+        if device is None:
+            try:
+                import torch
+                device = torch.cuda.current_device() if torch.cuda.is_available() else -1
+            except Exception:
+                device = -1
+        cfg.device = int(device)
+        self._lib = lib
+        self.n, self.batch, self.chi_cap = n_qubits, batch, chi_cap
+        h = ctypes.c_void_p()
+        st = ctypes.c_void_p(stream if isinstance(stream, int) else (stream.cuda_stream if stream is not None
+                                                                     else None))
+        _check(lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), st))
+        self._h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mpdo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- model -----------------------------------------------------------
+    def build_gates(self, wl, dt: Optional[float] = None):
+        """wl: a workloads.Workload with batch == self.batch."""
+        B, N = self.batch, self.n
+        assert wl.batch == B and wl.n == N
+        arrs = dict(h_x=_as(wl.h_x, np.float64), h_y=_as(wl.h_y, np.float64), h_z=_as(wl.h_z, np.float64),
+                    g0=_as(wl.g0, np.float64), g1=_as(wl.g1, np.float64), g2=_as(wl.g2, np.float64),
+                    J=_as(wl.J, np.float64), Jz=_as(wl.Jz, np.float64))
+        bi = _as([b[0] for b in wl.bonds], np.int32)
+        bj = _as([b[1] for b in wl.bonds], np.int32)
+        chi = _as(wl.chi_max, np.int32)
+        cut = _as(wl.cutoff, np.float64)
+        m = Model()
+        for k, a in arrs.items():
+            setattr(m, k, _ptr(a, ctypes.c_double))
+        m.n_bonds = len(wl.bonds)
+        m.bond_i, m.bond_j = _ptr(bi, ctypes.c_int), _ptr(bj, ctypes.c_int)
+        m.chi_max, m.cutoff = _ptr(chi, ctypes.c_int), _ptr(cut, ctypes.c_double)
+        init = None
+        if wl.init is not None:
+            init = "".join(s.lower() for s in wl.init).encode()
+        m.init_pauli = init
+        _check(self._lib.mpdo_build_gates(self._h, ctypes.byref(m), float(wl.dt if dt is None else dt)))
+
+    def step(self, n_steps: int = 1, check: bool = True):
+        rc = self._lib.mpdo_trotter_step(self._h, int(n_steps))
+        if check:
+            _check(rc)
+        return rc
+
+    # -- observables -----------------------------------------------------
+    def measure_1q(self, qubits: Sequence[int], comp: str = "Z", out=None):
+        """[B, nq] numpy array, or fills ``out`` (a CUDA torch tensor) in place."""
+        q = _as(qubits, np.int32)
+        if out is not None:
+            _check(self._lib.mpdo_measure_1q(self._h, _ptr(q, ctypes.c_int), len(q), comp.encode(),
+                                             ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        res = np.zeros((self.batch, len(q)))
+        _check(self._lib.mpdo_measure_1q(self._h, _ptr(q, ctypes.c_int), len(q), comp.encode(),
+                                         res.ctypes.data_as(ctypes.c_void_p), 0))
+        return res
+
+    def measure_2q(self, pairs, comps: str = "ZZ", connected: bool = True, out=None):
+        p = _as(pairs, np.int32).reshape(-1, 2)
+        if out is not None:
+            _check(self._lib.mpdo_measure_2q(self._h, _ptr(p, ctypes.c_int), len(p), comps.encode(),
+                                             int(connected), ctypes.c_void_p(out.data_ptr()), 1))
+            return out
+        res = np.zeros((self.batch, len(p)))
+        _check(self._lib.mpdo_measure_2q(self._h, _ptr(p, ctypes.c_int), len(p), comps.encode(), int(connected),
+                                         res.ctypes.data_as(ctypes.c_void_p), 0))
+        return res
+
+    # -- state and diagnostics ------------------------------------------
+    def status(self):
+        B, N = self.batch, self.n
+        st = np.zeros(B, np.int32)
+        md = np.zeros(B)
+        chi = np.zeros((B, N - 1), np.int32)
+        tr = np.zeros(B)
+        _check(self._lib.mpdo_status(self._h, _ptr(st, ctypes.c_int), _ptr(md, ctypes.c_double),
+                                     _ptr(chi, ctypes.c_int), _ptr(tr, ctypes.c_double)))
+        return {"status": st, "max_discarded": md, "chi": chi, "trace_before": tr}
+
+    def set_state(self, b: int, dims, tensors):
+        d = _as(dims, np.int32)
+        flat = np.concatenate([np.asarray(t, np.float64).reshape(-1) for t in tensors])
+        _check(self._lib.mpdo_set_state(self._h, int(b), _ptr(d, ctypes.c_int), _ptr(flat, ctypes.c_double)))
+
+    def get_state(self, b: int = 0):
+        d = np.zeros(self.n + 1, np.int32)
+        _check(self._lib.mpdo_get_state(self._h, int(b), _ptr(d, ctypes.c_int), None, 0))
+        tot = int(sum(int(d[p]) * 4 * int(d[p + 1]) for p in range(self.n)))
+        buf = np.zeros(max(tot, 1))
+        _check(self._lib.mpdo_get_state(self._h, int(b), _ptr(d, ctypes.c_int), _ptr(buf, ctypes.c_double), tot))
+        out, off = [], 0
+        for p in range(self.n):
+            sz = int(d[p]) * 4 * int(d[p + 1])
+            out.append(buf[off:off + sz].reshape(int(d[p]), 4, int(d[p + 1])).copy())
+            off += sz
+        return [int(x) for x in d], out
+
+    def op_counts(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.mpdo_op_counts(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
+
+    def gates(self, b: int = 0):
+        n_ops = self.op_counts()[0]
+        buf = np.zeros(n_ops * 256)
+        _check(self._lib.mpdo_gates(self._h, int(b), _ptr(buf, ctypes.c_double), len(buf)))
+        return buf.reshape(n_ops, 16, 16)
+
+    def profile(self, on: bool = True):
+        _check(self._lib.mpdo_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset: bool = False):
+        K = len(PROFILE_KINDS)
+        ms = np.zeros(K)
+        ln = np.zeros(K, np.int64)
+        fl = np.zeros(K)
+        _check(self._lib.mpdo_profile_read(self._h, _ptr(ms, ctypes.c_double), ln.ctypes.data_as(
+            ctypes.POINTER(ctypes.c_longlong)), _ptr(fl, ctypes.c_double), K, int(reset)))
+        return {k: {"ms": float(ms[i]), "launches": int(ln[i]), "flops": float(fl[i])}
+                for i, k in enumerate(PROFILE_KINDS)}
+
+    def rank_log(self, n_steps: int):
+        n_ops = self.op_counts()[0]
+        buf = np.zeros(self.batch * n_steps * n_ops, np.int32)
+        _check(self._lib.mpdo_rank_log(self._h, _ptr(buf, ctypes.c_int), len(buf)))
+        return buf.reshape(self.batch, n_steps * n_ops)

@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP64 path |delta| <= 1e-10 on every observable at equal chi_max and
+cutoff (when both sides chose the same truncation ranks; otherwise the oracle
+is replayed with the GPU's ranks), gates <= 1e-14."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import workloads as W
+from oracle import dense, model, schedule, tebd
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2203_05871_gb300 import build as B
+    B.build()
+
+
+def solver_for(wl, chi_cap=None, **kw):
+    from paper_2203_05871_gb300 import Solver
+    s = Solver(wl.n, batch=wl.batch, chi_cap=chi_cap or int(max(wl.chi_max)), **kw)
+    s.build_gates(wl)
+    return s
+
+
+def all_pairs(n):
+    return [(i, j) for i in range(n) for j in range(i + 1, n)]
+
+
+def oracle_run(wl, b, steps, forced=None):
+    t = tebd.TEBD(wl, b)
+    t.run(steps, forced_k=forced)
+    return t
+
+
+def compare_to_oracle(wl, steps, s, tol=TOL):
+    """Run the GPU solver s for `steps` and compare z and connected zz of every
+    instance with the oracle (frozen to the GPU's ranks if they differ)."""
+    s.step(steps)
+    gz = s.measure_1q(range(wl.n), "Z")
+    pairs = all_pairs(wl.n)
+    gzz = s.measure_2q(pairs, "ZZ", connected=True)
+    log = s.rank_log(steps)
+    worst = 0.0
+    for b in range(wl.batch):
+        o = oracle_run(wl, b, steps)
+        if list(o.k_log) != [int(k) for k in log[b]]:
+            o = oracle_run(wl, b, steps, forced=[int(k) for k in log[b]])
+        dz = np.abs(o.z() - gz[b]).max()
+        dzz = np.abs(o.zz_connected(pairs) - gzz[b]).max()
+        worst = max(worst, dz, dzz)
+        assert dz <= tol and dzz <= tol, (b, dz, dzz)
+    return worst
+
+
+# ---------------------------------------------------------------------------
+def test_gates_match_oracle():
+    wl = W.random_model(6, W.ring_bonds(6), 31, batch=2, chi_max=8)
+    s = solver_for(wl)
+    layers = schedule.step_layers(wl.n, wl.bonds)
+    for b in range(2):
+        ref = [G for gl in tebd.build_gates(wl, b, layers, wl.dt) for G in gl]
+        got = s.gates(b)
+        assert np.abs(np.array(ref) - got).max() <= 1e-14
+
+
+@pytest.mark.parametrize("bonds_fn", [W.chain_bonds, W.ring_bonds, lambda n: W.grid_snake_bonds(3, 2)])
+def test_untruncated_equals_dense_trotter(bonds_fn):
+    n = 6
+    wl = W.random_model(n, bonds_fn(n), 41, chi_max=64, cutoff=0.0, dt=0.07)
+    s = solver_for(wl)
+    s.step(3)
+    d = dense.DenseTrotter(wl).run(3)
+    gz = s.measure_1q(range(n), "Z")[0]
+    assert np.abs(gz - d.z()).max() <= 1e-12
+    pairs = all_pairs(n)
+    gzz = s.measure_2q(pairs, "ZZ", connected=False)[0]
+    assert np.abs(gzz - np.array([d.zz(i, j) for (i, j) in pairs])).max() <= 1e-12
+    st = s.status()
+    assert st["status"][0] == 0
+    assert abs(st["trace_before"][0] - 1.0) < 1e-12
+
+
+def test_chain8_chi32_forty_steps():
+    wl = W.chain8_fp64()
+    s = solver_for(wl)
+    worst = compare_to_oracle(wl, wl.steps, s)
+    assert worst <= TOL
+
+
+@pytest.mark.parametrize("bonds,n", [(W.ring_bonds(8), 8), (W.grid_snake_bonds(3, 3), 9)])
+def test_swap_routed_graphs(bonds, n):
+    wl = W.random_model(n, bonds, 53, chi_max=16, cutoff=1e-10, dt=0.05, with_all_terms=False)
+    s = solver_for(wl)
+    compare_to_oracle(wl, 4, s)
+
+
+def test_batched_uneven_chi():
+    wl = W.random_model(8, W.chain_bonds(8), 61, batch=4, chi_max=32, cutoff=1e-11)
+    wl.chi_max[:] = [4, 8, 16, 32]
+    s = solver_for(wl, chi_cap=32)
+    compare_to_oracle(wl, 5, s)
+
+
+def test_x_y_components_and_mixed_pairs():
+    wl = W.random_model(7, W.chain_bonds(7), 71, chi_max=64, cutoff=0.0)
+    s = solver_for(wl)
+    s.step(2)
+    o = oracle_run(wl, 0, 2, forced=[int(k) for k in s.rank_log(2)[0]])
+    for comp in "XYZ":
+        g = s.measure_1q(range(7), comp)[0]
+        ref = [o.state.expect_1q(i, comp) for i in range(7)]
+        assert np.abs(g - ref).max() <= TOL
+    pairs = [(0, 3), (5, 1), (2, 6), (4, 3)]
+    g = s.measure_2q(pairs, "XY", connected=True)[0]
+    for (i, j), v in zip(pairs, g):
+        ref = o.state.expect_2q(i, j, ("X", "Y")) - o.state.expect_1q(i, "X") * o.state.expect_1q(j, "Y")
+        assert abs(v - ref) <= TOL
+
+
+def test_initial_pauli_states():
+    wl = W.random_model(5, W.chain_bonds(5), 81, chi_max=16, cutoff=0.0,
+                        init=["+x", "-y", "+z", "-z", "-x"])
+    s = solver_for(wl)
+    g = {c: s.measure_1q(range(5), c)[0] for c in "XYZ"}
+    assert np.allclose(g["X"], [1, 0, 0, 0, -1]) and np.allclose(g["Y"], [0, -1, 0, 0, 0])
+    assert np.allclose(g["Z"], [0, 0, 1, -1, 0])
+    compare_to_oracle(wl, 2, s)
+
+
+# ---------------------------------------------------------------------------
+# full-size properties
+# ---------------------------------------------------------------------------
+def test_decoupled_grid40_chi512():
+    """J = 0 on the 4x10 snake (swap routing, chi_cap 512): chi stays 1 and every
+    qubit follows its own single-qubit evolution."""
+    wl = W.grid4x10_snake()
+    wl.J[:] = 0.0
+    s = solver_for(wl, chi_cap=512)
+    steps = 4
+    s.step(steps)
+    st = s.status()
+    assert st["chi"].max() == 1 and st["status"][0] == 0
+    z = s.measure_1q(range(wl.n), "Z")[0]
+    for q in range(wl.n):
+        Lp = model.site_generator(wl.h_x[0][q], 0.0, wl.h_z[0][q], wl.g0[0][q], 0.0, wl.g2[0][q])
+        c = sla.expm(Lp * steps * wl.dt) @ np.array([1.0, 0, 0, 1.0])
+        assert abs(z[q] - c[3]) < 1e-12
+
+
+def test_single_excitation_ring24_and_grid():
+    from tests.test_oracle_pins import single_excitation
+    for n, bonds in [(24, W.ring_bonds(24)), (40, W.grid_snake_bonds(10, 4))]:
+        rng = np.random.default_rng(n)
+        wl = W.uniform_model("sector", n, bonds, omega=rng.uniform(-1, 1, n), Omega=0.0, J=0.1, g0=0.02,
+                             g2=0.01, chi_max=64, cutoff=1e-13, dt=0.02, init=["-z"] + ["+z"] * (n - 1))
+        wl.J[0] = rng.uniform(0.2, 0.5, len(bonds))
+        T = 0.4
+        s = solver_for(wl)
+        s.step(int(round(T / wl.dt)))
+        R = single_excitation(n, bonds, wl.h_z[0], wl.J[0], wl.g0[0], wl.g2[0], 0, T).real
+        z = s.measure_1q(range(n), "Z")[0]
+        # second-order Trotter error at dt = 0.02: well below 1e-4 here
+        assert np.abs(z - (1 - 2 * np.diag(R))).max() < 1e-4
+
+
+def test_chi256_one_step_sampled():
+    """N=10 chain from a seeded random MPO at chi = 256 (1024 x 1024 SVDs):
+    one step on the GPU against the oracle on the same input."""
+    wl = W.chain20_precision()
+    n = 10
+    wl = W.uniform_model("chain10_chi256", n, W.chain_bonds(n), chi_max=256, cutoff=1e-10, dt=0.02)
+    dims, tens = W.random_mpo_state(n, 256, seed=7)
+    s = solver_for(wl, chi_cap=256)
+    s.set_state(0, dims, tens)
+    s.step(1)
+    log = [int(k) for k in s.rank_log(1)[0]]
+    st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
+    o = tebd.TEBD(wl, 0, state=st)
+    o.run(1, forced_k=log)
+    gz = s.measure_1q(range(n), "Z")[0]
+    assert np.abs(gz - o.z()).max() <= TOL
+    pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
+    g = s.measure_2q(pairs, "ZZ", connected=True)[0]
+    assert np.abs(g - o.zz_connected(pairs)).max() <= TOL
+
+
+def test_errors_are_codes_not_crashes():
+    from paper_2203_05871_gb300 import MpdoError, Solver
+    s = Solver(5, batch=1, chi_cap=8)
+    with pytest.raises(MpdoError):
+        s.step(1)                      # before build_gates
+    wl = W.random_model(5, W.chain_bonds(5), 3, chi_max=16)
+    with pytest.raises(MpdoError):
+        s.build_gates(wl)              # chi_max > chi_cap
+    wl = W.random_model(5, W.chain_bonds(5), 3, chi_max=8)
+    wl.g0[0, 2] = -1.0
+    with pytest.raises(MpdoError):
+        s.build_gates(wl)              # negative rate
+    wl.g0[0, 2] = 0.1
+    s.build_gates(wl)
+    with pytest.raises(MpdoError):
+        s.measure_2q([(1, 1)])
+    s.step(1)
