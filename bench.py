@@ -285,7 +285,7 @@ def main():
         s.step(1)
         z = s.measure_1q(range(wl.n), "Z")
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_value = world * n_ops * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_value = world * n_ops * args.e2e_steps / (e2e_ms / 1e3) if args.e2e_steps > 0 else None
 
     jac = prof["jacobi_svd"]
     achieved = jac["flops"] / (jac["ms"] / 1e3) / 1e12 if jac["ms"] > 0 else None
