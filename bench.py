@@ -305,6 +305,8 @@ def main():
         "gpu_launches": launches,
         "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                     for k, v in prof.items() if v["launches"]},
+        "jacobi_mean_sweeps": (prof["jacobi_svd"]["sweeps"] / prof["jacobi_svd"]["svds"]
+                               if prof["jacobi_svd"]["svds"] else None),
         "roofline": {"kernel": "jacobi_svd", "bound": "alu", "achieved": achieved,
                      "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
                      "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,

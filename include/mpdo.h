@@ -171,6 +171,9 @@ int mpdo_schedule(int n, int n_bonds, const int *bond_i, const int *bond_j, int 
  * up to kmax kinds (any pointer may be NULL) and, if reset != 0, zeroes them. */
 int mpdo_profile_enable(mpdo_ctx *ctx, int on);
 int mpdo_profile_read(mpdo_ctx *ctx, double *ms, long long *launches, double *flops, int kmax, int reset);
+/* Jacobi sweeps summed over the SVDs profiled since the last reset, and the
+ * number of those SVDs (profiling must be enabled). */
+int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds);
 
 /* Message of the last error on this thread ("" if none). */
 const char *mpdo_last_error(void);

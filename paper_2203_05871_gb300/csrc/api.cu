@@ -76,6 +76,9 @@ struct mpdo_ctx {
     // per-slot workspaces
     int slots = 0;
     double *d_thetap = nullptr, *d_W = nullptr, *d_Z = nullptr, *d_Yk = nullptr, *d_snorm = nullptr;
+    int* d_sweeps = nullptr;      // [slots] Jacobi sweeps of the last chunk
+    std::vector<int> h_sweeps;
+    long long prof_sweeps = 0, prof_svds = 0;
     OpDesc* d_desc = nullptr;
     OpDesc* h_desc = nullptr;     // pinned
     int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]
@@ -117,13 +120,14 @@ size_t site_elems(const mpdo_ctx* c) { return (size_t)c->cap * 4 * c->cap; }
 double* site(mpdo_ctx* c, int b, int p) { return c->d_sites + ((size_t)b * c->N + p) * site_elems(c); }
 
 int release_slots(mpdo_ctx* c) {
-    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync};
+    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
     c->d_desc = nullptr;
     c->d_cta = nullptr;
     c->d_sync = nullptr;
+    c->d_sweeps = nullptr;
     if (c->h_desc) cudaFreeHost(c->h_desc);
     if (c->h_cta) cudaFreeHost(c->h_cta);
     c->h_desc = nullptr;
@@ -149,6 +153,8 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_Z, (size_t)s * mat));
     CU(dalloc(&c->d_Yk, (size_t)s * c->cap * c->ld));
     CU(dalloc(&c->d_snorm, (size_t)s * c->ld));
+    CU(dalloc(&c->d_sweeps, (size_t)s));
+    c->h_sweeps.assign(s, 0);
     CU(dalloc(&c->d_desc, (size_t)s));
     const int gcap = std::max(c->jacobi_resident, s);
     CU(dalloc(&c->d_cta, (size_t)(2 * gcap + s)));
@@ -235,6 +241,8 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.status = c->d_status + b;
         d.max_disc = c->d_maxdisc + b;
         d.rank_log = nullptr;
+        d.jb = jacobi_block_rows(d.L + (d.transposed ? d.c : 0), d.c);
+        d.sweeps_out = c->d_sweeps + s;
         work[s] = (double)d.c * d.c * (double)d.L;
     }
     CU(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
@@ -250,7 +258,6 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     p_merge.stop();
 
     // Jacobi: share the co-resident CTAs among the ops in proportion to work
-    const int JW = jacobi_threads() / 32;
     const int R = c->jacobi_resident;
     double wsum = 0.0;
     for (double w : work) wsum += w;
@@ -258,9 +265,11 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     int total = 0;
     for (int s = 0; s < nops; ++s) {
         const OpDesc& d = c->h_desc[s];
-        const int need = std::max(1, ((d.c + 1) / 2 + JW - 1) / JW);
+        const int pairs = jacobi_pairs_per_round(d.c, d.jb);
         int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
-        g = std::max(1, std::min(need, g));
+        g = std::max(1, std::min(pairs, g));
+        const int passes = (pairs + g - 1) / g;      // block pairs per CTA per round
+        g = (pairs + passes - 1) / passes;           // fewest CTAs with that many passes
         G[s] = g;
         total += g;
     }
@@ -300,7 +309,13 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     // new bond dimensions back to the host (the next chunk's shapes depend on them)
     CU(cudaMemcpyAsync(c->h_dims.data(), c->d_dims, sizeof(int) * c->h_dims.size(), cudaMemcpyDeviceToHost,
                        c->st));
+    if (c->prof) CU(cudaMemcpyAsync(c->h_sweeps.data(), c->d_sweeps, sizeof(int) * nops, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
+    if (c->prof)
+        for (int s = 0; s < nops; ++s) {
+            c->prof_sweeps += c->h_sweeps[s];
+            c->prof_svds += 1;
+        }
     double fl_rec = 0.0;
     for (int s = 0; s < nops; ++s) {
         const OpDesc& d = c->h_desc[s];
@@ -795,12 +810,21 @@ int mpdo_profile_read(mpdo_ctx* c, double* ms, long long* launches, double* flop
         if (launches) launches[k] = c->prof_launch[k];
         if (flops) flops[k] = c->prof_flops[k];
     }
-    if (reset)
+    if (reset) {
         for (int k = 0; k < kProfKinds; ++k) {
             c->prof_ms[k] = 0.0;
             c->prof_launch[k] = 0;
             c->prof_flops[k] = 0.0;
         }
+        c->prof_sweeps = c->prof_svds = 0;
+    }
+    return MPDO_OK;
+}
+
+int mpdo_profile_sweeps(mpdo_ctx* c, long long* sweeps, long long* svds) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    if (sweeps) *sweeps = c->prof_sweeps;
+    if (svds) *svds = c->prof_svds;
     return MPDO_OK;
 }
 

@@ -40,6 +40,7 @@ struct OpDesc {
     int m, n;          // 4*cl, 4*cr
     int transposed;    // 1: Jacobi rows are the columns of theta~ (m > n), with Z
     int c, L;          // Jacobi problem: c rows of length L
+    int jb;            // Jacobi block size (rows per shared-memory block)
     int chi_max;
     double cutoff;
     const double* G;   // 16x16 gate, row-major G[(s1' s2'), (s1 s2)]
@@ -56,6 +57,7 @@ struct OpDesc {
     int* status;       // per-instance status word
     double* max_disc;  // per-instance max discarded weight
     int* rank_log;     // &log[b][step*n_ops + op] or nullptr
+    int* sweeps_out;   // Jacobi sweeps used (or nullptr)
 };
 
 // ---------------------------------------------------------------------------
@@ -79,6 +81,8 @@ struct JacobiPlan {
     int max_resident;    // co-resident capacity
 };
 int jacobi_threads();
+int jacobi_block_rows(int rowlen, int c);      // rows per block for rows of length rowlen
+int jacobi_pairs_per_round(int c, int b);      // block pairs per tournament round
 cudaError_t jacobi_max_resident(int* blocks);
 // d_cta_op[grid]: op index of each CTA; d_cta_rank[grid]: rank within its op;
 // d_group[nops]: CTAs per op.  d_sync: per-op counters (zeroed by the caller,

@@ -2,22 +2,28 @@
 //
 // App. B compresses |rho>> bond by bond from its Schmidt spectrum.  Each op
 // hands this kernel c rows of length L (the rows of theta~ when m <= n, or
-// its columns together with a c x c accumulator Z when m > n).  Plane
-// rotations from the left make the rows mutually orthogonal; row j then
-// equals s_j * v_j^T (or Z row j = v_j^T), which the truncation step reads.
+// its columns when m > n, then with a c x c accumulator Z whose rows turn
+// alongside).  Plane rotations from the left make the rows mutually
+// orthogonal; row j then equals s_j v_j^T (or Z row j = v_j^T), which the
+// truncation step reads.
 //
-// Parallel order: the round-robin ("circle") tournament pairs all c rows in
-// c' - 1 steps of c'/2 disjoint pairs (c' = c rounded up to even), so every
-// pair of rows meets once per sweep.  Each pair is handled by one warp: the
-// three inner products are reduced with warp shuffles, the rotation is
-// applied in a second pass.  The CTAs that share an op meet in a counter
-// barrier after every step; every wait is bounded by a wall-clock limit and
-// gives up with MPDO_ST_TIMEOUT instead of hanging.  The kernel is launched
-// cooperatively, so all CTAs are co-resident.
+// Block-pair ordering.  The rows are cut into blocks of b rows (b chosen so
+// that two blocks, with their Z parts, fit in 128 KB of shared memory).  A
+// round-robin ("circle") tournament over the blocks meets every pair of
+// blocks once per sweep; in a round each CTA loads one or more block pairs
+// into shared memory, rotates every cross pair of rows (and, in the first
+// round of a sweep, every pair inside each block), and stores the blocks back
+// to their home rows.  One barrier per round orders the CTAs of an op; every
+// wait is bounded by a wall-clock limit after which the kernel records
+// MPDO_ST_TIMEOUT and returns.  The launch is cooperative (all CTAs resident).
+// Within a block pair one warp owns one pair of rows: the inner product is
+// reduced with warp shuffles, the rotation is applied in shared memory.
 //
 // Rotation (Rutishauser): a = |w_p|^2, b = |w_q|^2, g = w_p.w_q,
 // zeta = (b - a) / 2g, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q.
+// cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q,
+// and then |w_p|^2 = a - t g, |w_q|^2 = b + t g (recomputed from the row when
+// the update loses more than 90% of the old value, and at every sweep start).
 // A pair is skipped when |g| <= tol sqrt(a b) (tol = sqrt(L) eps unless set).
 // A row whose norm is at most eps * ||W||_F is numerically zero: it is set to
 // zero and never rotated (its direction is rounding noise).
@@ -32,7 +38,10 @@ namespace {
 
 constexpr int JW = 8;             // warps per CTA
 constexpr int JT = JW * 32;
-constexpr int kSyncWords = 8 + kMaxSweepsCap;   // per op: [0] arrivals [1] abort [8+s] rotations in sweep s
+constexpr int kRowBytes = 128 * 1024;                  // two blocks of rows in shared memory
+constexpr int kMaxB = 16;
+constexpr int kSmemBytes = kRowBytes + 4 * kMaxB * 8;  // rows + norms (2b) + row ids
+constexpr int kSyncWords = 8 + kMaxSweepsCap;          // per op: [0] arrivals [1] abort [8+s] rotations in sweep s
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -87,64 +96,120 @@ __device__ __forceinline__ int tour_player(int x, int step, int cp) {
     return x == 0 ? 0 : 1 + ((x - 1 + step) % (cp - 1));
 }
 
-// one warp: orthogonalise rows p and q; returns 1 if a rotation was applied
-__device__ int pair_rotate(double* wp, double* wq, int L, double* zp, double* zq, int c, double floor2,
-                           double tol, int lane) {
-    double a = 0.0, b = 0.0, g = 0.0;
-    for (int i = lane; i < L; i += 32) {
-        const double x = __ldcg(wp + i), y = __ldcg(wq + i);
-        a = fma(x, x, a);
-        b = fma(y, y, b);
-        g = fma(x, y, g);
+__device__ __forceinline__ double row_dot(const double* x, const double* y, int L, int lane) {
+    double s0 = 0.0, s1 = 0.0;
+    int i = lane;
+    for (; i + 32 < L; i += 64) {
+        s0 = fma(x[i], y[i], s0);
+        s1 = fma(x[i + 32], y[i + 32], s1);
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    g = warp_sum(g);
-    if (a <= floor2 || b <= floor2) {
-        if (a <= floor2)
-            for (int i = lane; i < L; i += 32) __stcg(wp + i, 0.0);
-        if (b <= floor2)
-            for (int i = lane; i < L; i += 32) __stcg(wq + i, 0.0);
+    if (i < L) s0 = fma(x[i], y[i], s0);
+    return warp_sum(s0 + s1);
+}
+
+struct Ctx {
+    double* rows;     // [2b][rowlen] in shared memory
+    double* nrm;      // [2b]
+    int* rid;         // [2b] global row index or -1
+    int rowlen, L;    // row length in smem (W part + Z part), W part length
+    double floor2, tol;
+};
+
+// One warp: rows p, q (shared-memory slots).  Returns 1 if it rotated.
+__device__ int pair_rotate(const Ctx& C, int p, int q, int lane) {
+    if (C.rid[p] < 0 || C.rid[q] < 0) return 0;
+    double* rp = C.rows + (size_t)p * C.rowlen;
+    double* rq = C.rows + (size_t)q * C.rowlen;
+    const double a = C.nrm[p], b = C.nrm[q];
+    if (a <= C.floor2 || b <= C.floor2) {
+        if (a <= C.floor2 && a != 0.0) {
+            for (int i = lane; i < C.L; i += 32) rp[i] = 0.0;
+            __syncwarp();
+            if (lane == 0) C.nrm[p] = 0.0;
+        }
+        if (b <= C.floor2 && b != 0.0) {
+            for (int i = lane; i < C.L; i += 32) rq[i] = 0.0;
+            __syncwarp();
+            if (lane == 0) C.nrm[q] = 0.0;
+        }
+        __syncwarp();
         return 0;
     }
-    if (g == 0.0 || fabs(g) <= tol * sqrt(a) * sqrt(b)) return 0;
+    const double g = row_dot(rp, rq, C.L, lane);
+    if (g == 0.0 || fabs(g) <= C.tol * sqrt(a) * sqrt(b)) return 0;
     const double zeta = (b - a) / (2.0 * g);
     const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
     const double cs = 1.0 / sqrt(1.0 + t * t);
     const double sn = cs * t;
-    for (int i = lane; i < L; i += 32) {
-        const double x = __ldcg(wp + i), y = __ldcg(wq + i);
-        __stcg(wp + i, cs * x - sn * y);
-        __stcg(wq + i, sn * x + cs * y);
+    for (int i = lane; i < C.rowlen; i += 32) {
+        const double x = rp[i], y = rq[i];
+        rp[i] = fma(cs, x, -sn * y);
+        rq[i] = fma(sn, x, cs * y);
     }
-    if (zp) {
-        for (int i = lane; i < c; i += 32) {
-            const double x = __ldcg(zp + i), y = __ldcg(zq + i);
-            __stcg(zp + i, cs * x - sn * y);
-            __stcg(zq + i, sn * x + cs * y);
-        }
+    __syncwarp();
+    double na = a - t * g, nb = b + t * g;
+    if (na < 0.1 * a) na = row_dot(rp, rp, C.L, lane);
+    if (nb < 0.1 * b) nb = row_dot(rq, rq, C.L, lane);
+    if (lane == 0) {
+        C.nrm[p] = na;
+        C.nrm[q] = nb;
     }
+    __syncwarp();
     return 1;
 }
 
-__global__ void __launch_bounds__(JT) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
-                                                    const int* group, unsigned* sync, int max_sweeps, double tol_in,
-                                                    unsigned long long timeout_ns, int ld) {
+// All pairs inside slots [base, base+b) of one block (circle method), for
+// both blocks at once; then all cross pairs between the two blocks.
+__device__ int process_block_pair(const Ctx& C, int b, bool intra, int warp, int lane) {
+    int rot = 0;
+    if (intra && b > 1) {
+        const int bp = b + (b & 1);
+        for (int t = 0; t < bp - 1; ++t) {
+            for (int x = warp; x < bp; x += JW) {   // x < bp/2: block 0, else block 1
+                const int blk = x < bp / 2 ? 0 : 1;
+                const int y = x % (bp / 2);
+                const int P = tour_player(y, t, bp), Q = tour_player(bp - 1 - y, t, bp);
+                if (P >= b || Q >= b) continue;
+                rot += pair_rotate(C, blk * b + min(P, Q), blk * b + max(P, Q), lane);
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = 0; t < b; ++t) {
+        for (int i = warp; i < b; i += JW) rot += pair_rotate(C, i, b + (i + t) % b, lane);
+        __syncthreads();
+    }
+    return rot;
+}
+
+__global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
+                                                       const int* group, unsigned* sync, int max_sweeps,
+                                                       double tol_in, unsigned long long timeout_ns, int ld) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int op = cta_op[blockIdx.x];
     const int g = cta_rank[blockIdx.x];
     const int G = group[op];
     const OpDesc& d = descs[op];
     unsigned* sw = sync + (size_t)op * kSyncWords;
-    const int c = d.c, L = d.L;
+    const int c = d.c, L = d.L, b = d.jb;
     double* W = d.W;
     double* Z = d.transposed ? d.Z : nullptr;
+    const int zl = Z ? c : 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gw = g * JW + warp, NW = G * JW;
     unsigned gen = 0;
     __shared__ double s_floor2;
+    __shared__ int s_conv;
 
-    // Z = I and row norms
-    for (int row = gw; row < c; row += NW) {
+    Ctx C;
+    C.rowlen = L + zl;
+    C.L = L;
+    C.rows = reinterpret_cast<double*>(smem_raw);
+    C.nrm = C.rows + (size_t)2 * b * C.rowlen;
+    C.rid = reinterpret_cast<int*>(C.nrm + 2 * b);
+    C.tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * DBL_EPSILON;
+
+    // Z = I and the squared row norms (for the zero floor)
+    for (int row = g * JW + warp; row < c; row += G * JW) {
         const double* w = W + (size_t)row * ld;
         double a = 0.0;
         for (int i = lane; i < L; i += 32) {
@@ -163,32 +228,73 @@ __global__ void __launch_bounds__(JT) jacobi_kernel(const OpDesc* descs, const i
         s_floor2 = DBL_EPSILON * DBL_EPSILON * f;
     }
     __syncthreads();
+    C.floor2 = s_floor2;
     {
-        const double floor2 = s_floor2;
-        const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * DBL_EPSILON;
-        const int cp = c + (c & 1);
-        const int npairs = cp / 2;
-        int sweeps = max_sweeps < kMaxSweepsCap ? max_sweeps : kMaxSweepsCap;
-        bool converged = (c <= 1);
-        for (int sweep = 0; sweep < sweeps && !converged; ++sweep) {
+        const int nb = (c + b - 1) / b;
+        const int nbp = nb + (nb & 1);
+        const int npair = nbp / 2;
+        const int sweeps = max_sweeps < kMaxSweepsCap ? max_sweeps : kMaxSweepsCap;
+        int conv = (c <= 1);
+        int used = 0;
+        for (int sweep = 0; sweep < sweeps && !conv; ++sweep) {
             int rot = 0;
-            for (int step = 0; step < cp - 1; ++step) {
-                for (int i = gw; i < npairs; i += NW) {
-                    const int P = tour_player(i, step, cp), Q = tour_player(cp - 1 - i, step, cp);
-                    if (P >= c || Q >= c) continue;
-                    const int p = P < Q ? P : Q, q = P < Q ? Q : P;
-                    rot += pair_rotate(W + (size_t)p * ld, W + (size_t)q * ld, L,
-                                       Z ? Z + (size_t)p * ld : nullptr, Z ? Z + (size_t)q * ld : nullptr, c,
-                                       floor2, tol, lane);
+            for (int r = 0; r < nbp - 1; ++r) {
+                for (int i = g; i < npair; i += G) {
+                    const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
+                    const int bl[2] = {P < Q ? P : Q, P < Q ? Q : P};
+                    // load the two blocks (slot s < b: block bl[0]; s >= b: block bl[1])
+                    for (int s = warp; s < 2 * b; s += JW) {
+                        const int blk = bl[s / b];
+                        const int row = blk * b + (s % b);
+                        const bool ok = blk < nb && row < c;
+                        double* dst = C.rows + (size_t)s * C.rowlen;
+                        if (ok) {
+                            const double* w = W + (size_t)row * ld;
+                            for (int k = lane; k < L; k += 32) dst[k] = __ldcg(w + k);
+                            if (Z)
+                                for (int k = lane; k < c; k += 32) dst[L + k] = __ldcg(Z + (size_t)row * ld + k);
+                            __syncwarp();
+                            double nv;
+                            if (r == 0)
+                                nv = row_dot(dst, dst, L, lane);   // fresh norms at the start of a sweep
+                            else
+                                nv = __ldcg(d.snorm + row);
+                            if (lane == 0) {
+                                C.nrm[s] = nv;
+                                C.rid[s] = row;
+                            }
+                        } else if (lane == 0) {
+                            C.nrm[s] = 0.0;
+                            C.rid[s] = -1;
+                        }
+                    }
+                    __syncthreads();
+                    rot += process_block_pair(C, b, r == 0, warp, lane);
+                    // store back
+                    for (int s = warp; s < 2 * b; s += JW) {
+                        const int row = C.rid[s];
+                        if (row < 0) continue;
+                        const double* src = C.rows + (size_t)s * C.rowlen;
+                        double* w = W + (size_t)row * ld;
+                        for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
+                        if (Z)
+                            for (int k = lane; k < c; k += 32) __stcg(Z + (size_t)row * ld + k, src[L + k]);
+                        if (lane == 0) __stcg(d.snorm + row, C.nrm[s]);
+                    }
+                    __syncthreads();
                 }
-                if (step == cp - 2 && lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
+                if (r == nbp - 2 && lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
                 if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             }
-            converged = (ld_acquire(&sw[8 + sweep]) == 0u);
-            // every CTA must read the count before anyone starts the next sweep's counter;
-            // counters are per sweep, so no reset is needed.
+            if (threadIdx.x == 0) s_conv = (ld_acquire(&sw[8 + sweep]) == 0u);
+            __syncthreads();
+            conv = s_conv;
+            used = sweep + 1;
         }
-        if (!converged && g == 0 && threadIdx.x == 0) atomicOr(d.status, (int)MPDO_ST_NOCONV);
+        if (g == 0 && threadIdx.x == 0) {
+            if (d.sweeps_out) *d.sweeps_out = used;
+            if (!conv) atomicOr(d.status, (int)MPDO_ST_NOCONV);
+        }
     }
     return;
 timeout:
@@ -200,13 +306,27 @@ timeout:
 int jacobi_threads() { return JT; }
 size_t jacobi_sync_words_per_op() { return kSyncWords; }
 
+int jacobi_block_rows(int rowlen, int c) {
+    int b = kMaxB;
+    while (b > 1 && (size_t)2 * b * rowlen * sizeof(double) > (size_t)kRowBytes) b >>= 1;
+    while (b > 1 && b >= c) b >>= 1;   // at least two blocks when c > 1
+    return b;
+}
+
+int jacobi_pairs_per_round(int c, int b) {
+    const int nb = (c + b - 1) / b;
+    return (nb + (nb & 1)) / 2;
+}
+
 cudaError_t jacobi_max_resident(int* blocks) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JT, 0);
+    e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JT, kSmemBytes);
     if (e != cudaSuccess) return e;
     *blocks = sms * per_sm;
     return cudaSuccess;
@@ -219,7 +339,7 @@ cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, c
     if (grid <= 0) return cudaSuccess;
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
                     (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
-    return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JT), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JT), args, kSmemBytes, st);
 }
 
 }  // namespace mpdo

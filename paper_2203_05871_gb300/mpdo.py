@@ -79,6 +79,8 @@ def load_library(path: str = LIB_PATH):
         "mpdo_profile_enable": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_profile_read": (ctypes.c_int, [vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, ctypes.c_int,
                                              ctypes.c_int]),
+        "mpdo_profile_sweeps": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong),
+                                               ctypes.POINTER(ctypes.c_longlong)]),
         "mpdo_last_error": (ctypes.c_char_p, []),
         "mpdo_destroy": (None, [vp]),
     }
@@ -94,7 +96,7 @@ def exported_symbols() -> list[str]:
     """Names declared in include/mpdo.h (for the export test)."""
     return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
-            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read",
+            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read", "mpdo_profile_sweeps",
             "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -282,14 +284,19 @@ class Solver:
         _check(self._lib.mpdo_profile_enable(self._h, int(on)))
 
     def profile_read(self, reset: bool = False):
+        sw, sv = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.mpdo_profile_sweeps(self._h, ctypes.byref(sw), ctypes.byref(sv)))
         K = len(PROFILE_KINDS)
         ms = np.zeros(K)
         ln = np.zeros(K, np.int64)
         fl = np.zeros(K)
         _check(self._lib.mpdo_profile_read(self._h, _ptr(ms, ctypes.c_double), ln.ctypes.data_as(
             ctypes.POINTER(ctypes.c_longlong)), _ptr(fl, ctypes.c_double), K, int(reset)))
-        return {k: {"ms": float(ms[i]), "launches": int(ln[i]), "flops": float(fl[i])}
-                for i, k in enumerate(PROFILE_KINDS)}
+        out = {k: {"ms": float(ms[i]), "launches": int(ln[i]), "flops": float(fl[i])}
+               for i, k in enumerate(PROFILE_KINDS)}
+        out["jacobi_svd"]["sweeps"] = int(sw.value)
+        out["jacobi_svd"]["svds"] = int(sv.value)
+        return out
 
     def rank_log(self, n_steps: int):
         n_ops = self.op_counts()[0]
