@@ -175,6 +175,29 @@ int mpdo_profile_read(mpdo_ctx *ctx, double *ms, long long *launches, double *fl
  * number of those SVDs (profiling must be enabled). */
 int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds);
 
+/* mpdo_measure_1q without any device allocation, on a state held in the
+ * caller's device memory.  For callers that cannot call cudaMalloc: code that
+ * runs while a stream is being captured into a CUDA graph, or frameworks that
+ * give all device memory to their own allocator up front.  The paper has no
+ * counterpart; it is the same computation as mpdo_measure_1q.
+ *   sites   device, [batch][n_qubits][chi_cap][4][chi_cap] doubles, the site
+ *           tensors (l, a, r) of each instance (the layout libmpdo keeps)
+ *   dims    device, [batch][n_qubits+1] ints, bond dimensions, dims[0] =
+ *           dims[n_qubits] = 1, each in [1, chi_cap]
+ *   qubits  device, [nq] ints in [0, n_qubits)
+ *   out     device, [batch][nq] doubles: <sigma^comp_q> / tr rho
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL = default stream)
+ * Scratch: a static device array of 2^18 doubles (2 MiB) that every device
+ * loading the library keeps until the process exits; sizes with
+ * 2 * batch * (n_qubits + 1) * chi_cap > 2^18 are rejected with ECAPACITY.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current): make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU race on it.  Asynchronous: returns after
+ * queuing the kernels; EINVAL / ECAPACITY / ECUDA with mpdo_last_error(). */
+int mpdo_measure_1q_noalloc(const double *sites, const int *dims, int n_qubits, int batch, int chi_cap,
+                            const int *qubits, int nq, char comp, double *out, void *cuda_stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *mpdo_last_error(void);
 

@@ -17,6 +17,13 @@ using namespace mpdo;
 namespace {
 
 thread_local std::string g_err;
+}  // namespace
+
+namespace mpdo {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace mpdo
+
+namespace {
 constexpr int kProfKinds = 7;
 enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6 };
 

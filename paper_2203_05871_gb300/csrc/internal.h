@@ -24,6 +24,9 @@ struct Op {
 };
 using Layer = std::vector<Op>;
 
+// Sets the message returned by mpdo_last_error() on this thread.
+void set_last_error(const std::string& msg);
+
 // Builds the layers of one second-order step; returns "" or an error message.
 std::string build_schedule(int n, const std::vector<int>& bi, const std::vector<int>& bj,
                            std::vector<Layer>& layers, std::vector<double>& weights);

@@ -81,6 +81,8 @@ def load_library(path: str = LIB_PATH):
                                              ctypes.c_int]),
         "mpdo_profile_sweeps": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong),
                                                ctypes.POINTER(ctypes.c_longlong)]),
+        "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
+                                                   ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_last_error": (ctypes.c_char_p, []),
         "mpdo_destroy": (None, [vp]),
     }
@@ -96,7 +98,7 @@ def exported_symbols() -> list[str]:
     """Names declared in include/mpdo.h (for the export test)."""
     return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
-            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read", "mpdo_profile_sweeps",
+            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc",
             "mpdo_last_error", "mpdo_destroy"]
 
 
