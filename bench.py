@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain20_chi256")
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "both"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--probe-peaks", action="store_true")
@@ -50,17 +50,22 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
+# Schmidt-value grading of the synthetic start: exp(-DECAY * r) on bond index r,
+# i.e. about 1e-5 between the first and the 256th value (a discarded weight
+# near the 1e-10 cutoff at chi = 256)
+DECAY = 0.045
+
+
 def make_workload(name):
     import workloads as W
-    if name == "chain20_chi256":
-        wl = W.chain20_precision(chi_max=256)
-        dims, tens = W.random_mpo_state(wl.n, 256, seed=2203058712 + 1)
-        return wl, dims, tens, 256
-    if name == "chain20_chi128":
-        wl = W.chain20_precision(chi_max=128)
-        dims, tens = W.random_mpo_state(wl.n, 128, seed=2203058712 + 1)
-        return wl, dims, tens, 128
-    raise SystemExit(f"unknown workload {name}")
+    table = {"chain20_chi256": (256, DECAY), "chain20_chi256_flat": (256, 0.0),
+             "chain20_chi128": (128, DECAY), "chain20_chi64": (64, DECAY)}
+    if name not in table:
+        raise SystemExit(f"unknown workload {name}")
+    chi, decay = table[name]
+    wl = W.chain20_precision(chi_max=chi)
+    dims, tens = W.random_mpo_state(wl.n, chi, seed=2203058712 + 1, decay=decay)
+    return wl, dims, tens, chi
 
 
 class ClockSampler:
@@ -217,31 +222,15 @@ def probe_peaks():
 
 
 # ---------------------------------------------------------------------------
-def main():
-    args = parse()
-    if args.probe_peaks:
-        return probe_peaks()
-    if args.impl == "reference":
-        return run_reference(args)
+def run_arm(args, precision, world, dist, local):
+    """Time args.steps Trotter steps of one precision; returns a result dict."""
     import numpy as np
     import torch
-    from paper_2203_05871_gb300 import Solver, build as B
+    from paper_2203_05871_gb300 import FP64, MIXED_TF32, Solver
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    if rank == 0 or world == 1:
-        B.build()
-    if dist:
-        dist.barrier()
     wl, dims, tens, cap = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    s = Solver(wl.n, batch=1, chi_cap=cap, stream=stream)
+    s = Solver(wl.n, batch=1, chi_cap=cap, stream=stream, precision=FP64 if precision == "fp64" else MIXED_TF32)
     s.build_gates(wl)
     s.set_state(0, dims, tens)
     n_ops, n_swaps, _ = s.op_counts()
@@ -271,10 +260,7 @@ def main():
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    ms_per_step = ms / args.steps
-    value = world * n_ops * args.steps / (ms / 1e3)
     st = s.status()
-
     # end to end through the C ABI from host buffers (state in, observables out)
     flat_bytes = sum(int(np.asarray(t).size) for t in tens) * 8
     e2e_ms = 0.0
@@ -283,12 +269,46 @@ def main():
         t0 = time.perf_counter()
         s.set_state(0, dims, tens)
         s.step(1)
-        z = s.measure_1q(range(wl.n), "Z")
+        s.measure_1q(range(wl.n), "Z")
         e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_value = world * n_ops * args.e2e_steps / (e2e_ms / 1e3) if args.e2e_steps > 0 else None
+    s.close()
+    return {"wl": wl, "cap": cap, "n_ops": n_ops, "n_swaps": n_swaps, "ms": ms, "prof": prof, "status": st,
+            "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
+
+def main():
+    args = parse()
+    if args.probe_peaks:
+        return probe_peaks()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2203_05871_gb300 import build as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    arms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    res = {p: run_arm(args, p, world, dist, local) for p in arms}
+    head = res["mixed"] if "mixed" in res else res["fp64"]
+    hp = "mixed" if "mixed" in res else "fp64"
+    wl, cap, n_ops = head["wl"], head["cap"], head["n_ops"]
+    ms_per_step = head["ms"] / args.steps
+    value = world * n_ops * args.steps / (head["ms"] / 1e3)
+    e2e_value = world * n_ops * args.e2e_steps / (head["e2e_ms"] / 1e3) if args.e2e_steps > 0 else None
+    prof = head["prof"]
     jac = prof["jacobi_svd"]
-    achieved = jac["flops"] / (jac["ms"] / 1e3) / 1e12 if jac["ms"] > 0 else None
+    svd_ms = jac["ms"] + prof["jacobi_fp32"]["ms"] + prof["precond_gemm"]["ms"]
+    achieved = jac["flops"] / (svd_ms / 1e3) / 1e12 if svd_ms > 0 else None
     launches = sum(v["launches"] for v in prof.values())
     line = {
         "metric": "gate_applications_per_sec", "value": value, "unit": "gate-applications/s",
@@ -297,30 +317,39 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "n_qubits": wl.n, "chi_max": cap, "cutoff": float(wl.cutoff[0]),
-                   "dt": wl.dt, "ops_per_step": n_ops, "swaps_per_step": n_swaps, "precision": args.precision,
+                   "dt": wl.dt, "ops_per_step": n_ops, "swaps_per_step": head["n_swaps"], "precision": hp,
                    "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed steps",
-                   "start": "seeded random MPO at chi=256"},
-        "e2e": {"value": e2e_value, "unit": "gate-applications/s", "h2d_bytes_per_step": flat_bytes,
+                   "start": "seeded random MPO at chi_max, Schmidt grading exp(-%.3f r)" % (
+                       DECAY if "flat" not in args.workload else 0.0)},
+        "e2e": {"value": e2e_value, "unit": "gate-applications/s", "h2d_bytes_per_step": head["flat_bytes"],
                 "d2h_bytes_per_step": wl.n * 8},
         "gpu_launches": launches,
         "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                     for k, v in prof.items() if v["launches"]},
-        "jacobi_mean_sweeps": (prof["jacobi_svd"]["sweeps"] / prof["jacobi_svd"]["svds"]
-                               if prof["jacobi_svd"]["svds"] else None),
-        "roofline": {"kernel": "jacobi_svd", "bound": "alu", "achieved": achieved,
-                     "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
-                     "traffic": None,
+        "jacobi_mean_sweeps": (jac["sweeps"] / jac["svds"] if jac["svds"] else None),
+        "jacobi_mean_sweeps_fp32": (jac["sweeps_fp32"] / jac["svds"] if jac["svds"] else None),
+        "roofline": {"kernel": "truncation SVD (jacobi_svd%s)" % (" + jacobi_fp32 + precond_gemm" if hp == "mixed"
+                                                                    else ""),
+                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None, "traffic": None,
                      "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
-                             "FP64 of GB300 (no measured FP64 peak in MEASURED_PEAKS.json)"},
-        "clocks": clk.summary(),
-        "status": int(st["status"][0]), "chi_max_seen": int(st["chi"].max()),
+                             "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
+                             "MEASURED_PEAKS.json)"},
+        "clocks": head["clocks"],
+        "status": int(head["status"]["status"][0]), "chi_max_seen": int(head["status"]["chi"].max()),
     }
+    if "fp64" in res and hp != "fp64":
+        f = res["fp64"]
+        line["fp64_path"] = {"value": world * f["n_ops"] * args.steps / (f["ms"] / 1e3),
+                             "ms_per_step": f["ms"] / args.steps,
+                             "jacobi_mean_sweeps": (f["prof"]["jacobi_svd"]["sweeps"] / f["prof"]["jacobi_svd"]["svds"]
+                                                    if f["prof"]["jacobi_svd"]["svds"] else None),
+                             "clocks": f["clocks"]}
+        line["speedup_mixed_vs_fp64"] = f["ms"] / head["ms"]
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:
         print(json.dumps(line))
-    s.close()
     if dist:
         dist.destroy_process_group()
 

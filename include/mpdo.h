@@ -163,17 +163,19 @@ int mpdo_schedule(int n, int n_bonds, const int *bond_i, const int *bond_j, int 
 
 /* Kernel timing.  mpdo_profile_enable(ctx, 1) brackets every kernel launch
  * of the step with CUDA events on the context stream and accumulates, per
- * kernel kind k (0 merge+gate, 1 Jacobi SVD, 2 truncate, 3 reconstruct,
- * 4 trace, 5 environments/measure, 6 gate build), the device time in ms,
+ * kernel kind k (0 merge+gate, 1 Jacobi SVD (FP64), 2 truncate, 3 reconstruct,
+ * 4 trace, 5 environments/measure, 6 gate build, 7 FP32 preconditioning
+ * Jacobi, 8 preconditioner GEMMs), the device time in ms,
  * the number of launches and the algorithmic flops of the work launched
  * (merge 32 cl cm cr, gate 512 cl cr, SVD 21 n^3 with n = 4 max(cl, cr),
  * reconstruct 32 cl cr k; 0 for the other kinds).  mpdo_profile_read copies
  * up to kmax kinds (any pointer may be NULL) and, if reset != 0, zeroes them. */
 int mpdo_profile_enable(mpdo_ctx *ctx, int on);
 int mpdo_profile_read(mpdo_ctx *ctx, double *ms, long long *launches, double *flops, int kmax, int reset);
-/* Jacobi sweeps summed over the SVDs profiled since the last reset, and the
- * number of those SVDs (profiling must be enabled). */
-int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds);
+/* FP64 Jacobi sweeps summed over the SVDs profiled since the last reset, the
+ * number of those SVDs, and the FP32 preconditioning sweeps (mixed precision
+ * only).  Profiling must be enabled. */
+int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds, long long *sweeps_fp32);
 
 /* mpdo_measure_1q without any device allocation, on a state held in the
  * caller's device memory.  For callers that cannot call cudaMalloc: code that

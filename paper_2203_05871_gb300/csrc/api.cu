@@ -24,8 +24,9 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace mpdo
 
 namespace {
-constexpr int kProfKinds = 7;
-enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6 };
+constexpr int kProfKinds = 9;
+enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6, K_JACOBI32 = 7,
+       K_GEMM = 8 };
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -84,8 +85,13 @@ struct mpdo_ctx {
     int slots = 0;
     double *d_thetap = nullptr, *d_W = nullptr, *d_Z = nullptr, *d_Yk = nullptr, *d_snorm = nullptr;
     int* d_sweeps = nullptr;      // [slots] Jacobi sweeps of the last chunk
+    bool mixed = false;           // mixed-precision SVD (FP32 preconditioning + FP64 finish)
+    double *d_W0 = nullptr, *d_E = nullptr, *d_Q = nullptr;
+    float *d_W32 = nullptr, *d_U32 = nullptr;
+    GemmDesc* d_gemm = nullptr;
+    GemmDesc* h_gemm = nullptr;   // pinned, [3][slots]
     std::vector<int> h_sweeps;
-    long long prof_sweeps = 0, prof_svds = 0;
+    long long prof_sweeps = 0, prof_svds = 0, prof_sweeps32 = 0;
     OpDesc* d_desc = nullptr;
     OpDesc* h_desc = nullptr;     // pinned
     int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]
@@ -127,10 +133,16 @@ size_t site_elems(const mpdo_ctx* c) { return (size_t)c->cap * 4 * c->cap; }
 double* site(mpdo_ctx* c, int b, int p) { return c->d_sites + ((size_t)b * c->N + p) * site_elems(c); }
 
 int release_slots(mpdo_ctx* c) {
-    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps};
+    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps,
+                    c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
+    c->d_W0 = c->d_E = c->d_Q = nullptr;
+    c->d_W32 = c->d_U32 = nullptr;
+    c->d_gemm = nullptr;
+    if (c->h_gemm) cudaFreeHost(c->h_gemm);
+    c->h_gemm = nullptr;
     c->d_desc = nullptr;
     c->d_cta = nullptr;
     c->d_sync = nullptr;
@@ -146,7 +158,8 @@ int release_slots(mpdo_ctx* c) {
 int alloc_slots(mpdo_ctx* c, int want) {
     release_slots(c);
     const size_t mat = (size_t)c->ld * c->ld;
-    const size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + c->ld) * sizeof(double);
+    size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + c->ld) * sizeof(double);
+    if (c->mixed) per_slot_bytes += 3 * mat * sizeof(double) + 2 * mat * sizeof(float);
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
     const size_t budget = free_b / 2;
@@ -164,10 +177,19 @@ int alloc_slots(mpdo_ctx* c, int want) {
     c->h_sweeps.assign(s, 0);
     CU(dalloc(&c->d_desc, (size_t)s));
     const int gcap = std::max(c->jacobi_resident, s);
-    CU(dalloc(&c->d_cta, (size_t)(2 * gcap + s)));
+    CU(dalloc(&c->d_cta, (size_t)2 * (2 * gcap + s)));
     CU(dalloc(&c->d_sync, (size_t)s * jacobi_sync_words_per_op()));
     CU(cudaMallocHost((void**)&c->h_desc, sizeof(OpDesc) * s));
-    CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * (2 * gcap + s)));
+    CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * 2 * (2 * gcap + s)));
+    if (c->mixed) {
+        CU(dalloc(&c->d_W0, (size_t)s * mat));
+        CU(dalloc(&c->d_E, (size_t)s * mat));
+        CU(dalloc(&c->d_Q, (size_t)s * mat));
+        CU(dalloc(&c->d_W32, (size_t)s * mat));
+        CU(dalloc(&c->d_U32, (size_t)s * mat));
+        CU(dalloc(&c->d_gemm, (size_t)3 * s));
+        CU(cudaMallocHost((void**)&c->h_gemm, sizeof(GemmDesc) * 3 * s));
+    }
     return MPDO_OK;
 }
 
@@ -248,8 +270,15 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.status = c->d_status + b;
         d.max_disc = c->d_maxdisc + b;
         d.rank_log = nullptr;
-        d.jb = jacobi_block_rows(d.L + (d.transposed ? d.c : 0), d.c);
+        d.jb = jacobi_block_rows(d.L + (d.transposed ? d.c : 0), d.c, 8);
+        d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
         d.sweeps_out = c->d_sweeps + s;
+        d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
+        d.W32 = c->mixed ? c->d_W32 + (size_t)s * mat : nullptr;
+        d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
+        d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
+        d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
+        d.Zinit = (c->mixed && d.transposed) ? d.Q : nullptr;
         work[s] = (double)d.c * d.c * (double)d.L;
     }
     CU(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
@@ -264,48 +293,91 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
     p_merge.stop();
 
-    // Jacobi: share the co-resident CTAs among the ops in proportion to work
-    const int R = c->jacobi_resident;
-    double wsum = 0.0;
-    for (double w : work) wsum += w;
-    std::vector<int> G(nops, 1);
-    int total = 0;
-    for (int s = 0; s < nops; ++s) {
-        const OpDesc& d = c->h_desc[s];
-        const int pairs = jacobi_pairs_per_round(d.c, d.jb);
-        int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
-        g = std::max(1, std::min(pairs, g));
-        const int passes = (pairs + g - 1) / g;      // block pairs per CTA per round
-        g = (pairs + passes - 1) / passes;           // fewest CTAs with that many passes
-        G[s] = g;
-        total += g;
-    }
-    while (total > R) {   // trim the largest groups until everything is co-resident
-        int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
-        if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident Jacobi CTAs");
-        G[arg]--;
-        total--;
-    }
-    int* h_op = c->h_cta;
-    int* h_rank = c->h_cta + total;
-    int* h_group = c->h_cta + 2 * total;
-    int t = 0;
-    for (int s = 0; s < nops; ++s) {
-        h_group[s] = G[s];
-        for (int g = 0; g < G[s]; ++g, ++t) {
-            h_op[t] = s;
-            h_rank[t] = g;
-        }
-    }
-    int* d_op = c->d_cta;
-    int* d_rank = c->d_cta + total;
-    int* d_group = c->d_cta + 2 * total;
-    CU(cudaMemcpyAsync(c->d_cta, c->h_cta, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
-    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
+    const int gcap = std::max(c->jacobi_resident, c->slots);
+    // Jacobi launch plan: share the co-resident CTAs among the ops in
+    // proportion to their work; h_cta/d_cta hold [op of each CTA | rank | CTAs per op]
+    auto plan = [&](bool fp32, int* hbase, int& total) -> int {
+        const int R = c->jacobi_resident;
+        double wsum = 0.0;
+        for (double w : work) wsum += w;
+        std::vector<int> G(nops, 1);
+        total = 0;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            const int pairs = jacobi_pairs_per_round(d.c, fp32 ? d.jb32 : d.jb);
+            int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
+            g = std::max(1, std::min(pairs, g));
+            const int passes = (pairs + g - 1) / g;      // block pairs per CTA per round
+            g = (pairs + passes - 1) / passes;           // fewest CTAs with that many passes
+            G[s] = g;
+            total += g;
+        }
+        while (total > R) {   // trim the largest groups until everything is co-resident
+            int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
+            if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident Jacobi CTAs");
+            G[arg]--;
+            total--;
+        }
+        int t = 0;
+        for (int s = 0; s < nops; ++s) {
+            hbase[2 * total + s] = G[s];
+            for (int g = 0; g < G[s]; ++g, ++t) {
+                hbase[t] = s;
+                hbase[total + t] = g;
+            }
+        }
+        return MPDO_OK;
+    };
+    auto run_jacobi = [&](bool fp32, int slot) -> int {
+        int total = 0;
+        int* hbase = c->h_cta + (size_t)slot * (2 * gcap + c->slots);
+        int* dbase = c->d_cta + (size_t)slot * (2 * gcap + c->slots);
+        int rc = plan(fp32, hbase, total);
+        if (rc) return rc;
+        CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
+        CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+        CU(launch_jacobi(c->d_desc, nops, dbase, dbase + total, dbase + 2 * total, c->d_sync, total,
+                         fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : c->cfg.jacobi_tol,
+                         timeout_ns, ld, fp32, c->st));
+        return MPDO_OK;
+    };
+    CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, c->st));
+    double fl_gemm = 0.0;
+    if (c->mixed) {
+        // FP32 preconditioning Jacobi on (W32 | U32)
+        ProfScope p_j32(c, K_JACOBI32);
+        int rc = run_jacobi(true, 1);
+        if (rc) return rc;
+        p_j32.stop();
+        // E = U U^T - I (FP64 accumulation of exact FP32 products),
+        // Q = U - E U / 2 (one Newton-Schulz step; E is ~1e-6 so FP32 suffices),
+        // W = Q W0 (FP64)
+        GemmDesc* g1 = c->h_gemm;
+        GemmDesc* g2 = c->h_gemm + c->slots;
+        GemmDesc* g3 = c->h_gemm + 2 * c->slots;
+        int maxc = 1, maxL = 1;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            maxc = std::max(maxc, d.c);
+            maxL = std::max(maxL, d.L);
+            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1};
+            g2[s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0};
+            g3[s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0};
+            fl_gemm += 2.0 * d.c * d.c * d.c * 2 + 2.0 * d.c * d.c * d.L;
+        }
+        CU(cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(GemmDesc) * 3 * c->slots, cudaMemcpyHostToDevice, c->st));
+        ProfScope p_gemm(c, K_GEMM);
+        CU(launch_gemm(c->d_gemm, nops, maxc, maxc, false, c->st));
+        CU(launch_gemm(c->d_gemm + c->slots, nops, maxc, maxc, true, c->st));
+        CU(launch_gemm(c->d_gemm + 2 * c->slots, nops, maxc, maxL, false, c->st));
+        p_gemm.stop();
+    }
     ProfScope p_jac(c, K_JACOBI);
-    CU(launch_jacobi(c->d_desc, nops, d_op, d_rank, d_group, c->d_sync, total, c->cfg.jacobi_max_sweeps,
-                     c->cfg.jacobi_tol, timeout_ns, ld, c->st));
+    {
+        int rc = run_jacobi(false, 0);
+        if (rc) return rc;
+    }
     p_jac.stop();
     ProfScope p_tr(c, K_TRUNC);
     CU(launch_truncate(c->d_desc, nops, cap, c->st));
@@ -320,7 +392,8 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     CU(cudaStreamSynchronize(c->st));
     if (c->prof)
         for (int s = 0; s < nops; ++s) {
-            c->prof_sweeps += c->h_sweeps[s];
+            c->prof_sweeps += c->h_sweeps[s] & 0xffff;
+            c->prof_sweeps32 += c->h_sweeps[s] >> 16;
             c->prof_svds += 1;
         }
     double fl_rec = 0.0;
@@ -330,6 +403,10 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     }
     prof_collect(c, K_MERGE, fl_merge);
     prof_collect(c, K_JACOBI, fl_svd);
+    if (c->mixed) {
+        prof_collect(c, K_JACOBI32, 0.0);
+        prof_collect(c, K_GEMM, fl_gemm);
+    }
     prof_collect(c, K_TRUNC, 0.0);
     prof_collect(c, K_RECON, fl_rec);
     for (int s = 0; s < nops; ++s) {
@@ -419,7 +496,8 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     if (cfg->n_qubits < 3) return fail(MPDO_EINVAL, "n_qubits must be >= 3");
     if (cfg->batch < 1) return fail(MPDO_EINVAL, "batch must be >= 1");
     if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
-    if (cfg->precision != MPDO_FP64) return fail(MPDO_EINVAL, "precision: only MPDO_FP64 is available in this build");
+    if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32 && cfg->precision != MPDO_MIXED_BF16X3)
+        return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
     if (cfg->storage != MPDO_STORE_F64) return fail(MPDO_EINVAL, "storage: only MPDO_STORE_F64 is available");
     if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
     if (cfg->jacobi_max_sweeps < 1 || cfg->jacobi_max_sweeps > kMaxSweepsCap)
@@ -431,6 +509,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     mpdo_ctx* c = new (std::nothrow) mpdo_ctx();
     if (!c) return fail(MPDO_ENOMEM, "host allocation failed");
     c->dev = dev;
+    c->mixed = cfg->precision != MPDO_FP64;
     c->cfg = *cfg;
     c->st = (cudaStream_t)cuda_stream;
     c->N = cfg->n_qubits;
@@ -823,15 +902,16 @@ int mpdo_profile_read(mpdo_ctx* c, double* ms, long long* launches, double* flop
             c->prof_launch[k] = 0;
             c->prof_flops[k] = 0.0;
         }
-        c->prof_sweeps = c->prof_svds = 0;
+        c->prof_sweeps = c->prof_svds = c->prof_sweeps32 = 0;
     }
     return MPDO_OK;
 }
 
-int mpdo_profile_sweeps(mpdo_ctx* c, long long* sweeps, long long* svds) {
+int mpdo_profile_sweeps(mpdo_ctx* c, long long* sweeps, long long* svds, long long* sweeps_fp32) {
     if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
     if (sweeps) *sweeps = c->prof_sweeps;
     if (svds) *svds = c->prof_svds;
+    if (sweeps_fp32) *sweeps_fp32 = c->prof_sweeps32;
     return MPDO_OK;
 }
 

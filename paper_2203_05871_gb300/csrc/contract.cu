@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(256) merge_gate_kernel(const OpDesc* descs, in
         const int row = l * 4 + s1, col = s2 * d.cr + r;
         d.thetap[(size_t)row * ld + col] = v;
         if (d.transposed)
-            d.W[(size_t)col * ld + row] = lam * v;
+            d.W0[(size_t)col * ld + row] = lam * v;
         else
-            d.W[(size_t)row * ld + col] = lam * v;
+            d.W0[(size_t)row * ld + col] = lam * v;
     }
 }
 

@@ -43,7 +43,8 @@ struct OpDesc {
     int m, n;          // 4*cl, 4*cr
     int transposed;    // 1: Jacobi rows are the columns of theta~ (m > n), with Z
     int c, L;          // Jacobi problem: c rows of length L
-    int jb;            // Jacobi block size (rows per shared-memory block)
+    int jb;            // Jacobi block size (rows per shared-memory block), FP64 pass
+    int jb32;          // same for the FP32 preconditioning pass
     int chi_max;
     double cutoff;
     const double* G;   // 16x16 gate, row-major G[(s1' s2'), (s1 s2)]
@@ -52,8 +53,14 @@ struct OpDesc {
     const double* lam_left;  // lambda_{p-1} (nullptr => 1)
     double* lam_out;   // lambda_p
     double* thetap;    // Theta'  m x n (ld)
+    double* W0;        // where merge writes theta~ (== W in the FP64 path)
     double* W;         // Jacobi rows: theta~ (m x n) or theta~^T (n x m)
     double* Z;         // c x c rotation accumulator when transposed
+    const double* Zinit;  // initial Z (nullptr => identity)
+    float* W32;        // mixed path: FP32 rows of the preconditioning Jacobi (c x L)
+    float* U32;        // mixed path: FP32 accumulated rotations (c x c)
+    double* E;         // mixed path: U32 U32^T - I (c x c)
+    double* Q;         // mixed path: orthogonalised U32 (c x c)
     double* Yk;        // k x n right singular vectors (rows), ld
     double* snorm;     // c row norms (scratch)
     int* k_out;        // new chi_p
@@ -84,18 +91,37 @@ struct JacobiPlan {
     int max_resident;    // co-resident capacity
 };
 int jacobi_threads();
-int jacobi_block_rows(int rowlen, int c);      // rows per block for rows of length rowlen
+int jacobi_block_rows(int rowlen, int c, int elem_bytes);   // rows per block for rows of length rowlen
 int jacobi_pairs_per_round(int c, int b);      // block pairs per tournament round
 cudaError_t jacobi_max_resident(int* blocks);
 // d_cta_op[grid]: op index of each CTA; d_cta_rank[grid]: rank within its op;
 // d_group[nops]: CTAs per op.  d_sync: per-op counters (zeroed by the caller,
 // layout documented in jacobi.cu).
+// fp32 = true: the FP32 preconditioning pass on (W32 | U32) (U32 starts as I,
+// W32 is filled from W0, scaled); false: the FP64 pass on (W | Z).
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, cudaStream_t st);
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st);
 size_t jacobi_sync_words_per_op();
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+
+// C = alpha * A op(B) + beta * D (- I): see gemm.cu
+struct GemmDesc {
+    int M, N, K;
+    const void* A;
+    int lda, a_f32;
+    const void* B;
+    int ldb, b_f32, b_trans;
+    double* C;
+    int ldc;
+    double alpha, beta;
+    const void* D;
+    int ldd, d_f32;
+    int sub_identity;
+};
+cudaError_t launch_gemm(const GemmDesc* d_desc, int count, int max_m, int max_n, bool fp32_compute,
+                        cudaStream_t st);
 
 cudaError_t launch_trace_normalize(double* sites, const int* dims, int n, int B, int chi_cap,
                                    int force, double* trace_out, int* status, cudaStream_t st);

@@ -24,7 +24,12 @@
 // cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q,
 // and then |w_p|^2 = a - t g, |w_q|^2 = b + t g (recomputed from the row when
 // the update loses more than 90% of the old value, and at every sweep start).
-// A pair is skipped when |g| <= tol sqrt(a b) (tol = sqrt(L) eps unless set).
+// A pair is skipped when g^2 <= tol^2 a b (tol = sqrt(L) eps unless set).
+//
+// The same kernel, instantiated for float, is the preconditioning pass of the
+// mixed-precision SVD: it orthogonalises an FP32 copy of the rows (scaled to
+// unit mean square norm) and accumulates its rotations in U32; the FP64 pass
+// then starts from Q W with Q the FP64-orthogonalised U32 (see api.cu).
 // A row whose norm is at most eps * ||W||_F is numerically zero: it is set to
 // zero and never rotated (its direction is rounding noise).
 #include <float.h>
@@ -39,7 +44,7 @@ namespace {
 constexpr int JW = 8;             // warps per CTA
 constexpr int JT = JW * 32;
 constexpr int kRowBytes = 128 * 1024;                  // two blocks of rows in shared memory
-constexpr int kMaxB = 16;
+constexpr int kMaxB = 32;
 constexpr int kSmemBytes = kRowBytes + 4 * kMaxB * 8;  // rows + norms (2b) + row ids
 constexpr int kSyncWords = 8 + kMaxSweepsCap;          // per op: [0] arrivals [1] abort [8+s] rotations in sweep s
 
@@ -86,7 +91,8 @@ __device__ bool op_barrier(unsigned* sw, int G, unsigned& gen, unsigned long lon
     return s_ok != 0;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -96,8 +102,9 @@ __device__ __forceinline__ int tour_player(int x, int step, int cp) {
     return x == 0 ? 0 : 1 + ((x - 1 + step) % (cp - 1));
 }
 
-__device__ __forceinline__ double row_dot(const double* x, const double* y, int L, int lane) {
-    double s0 = 0.0, s1 = 0.0;
+template <typename T>
+__device__ __forceinline__ T row_dot(const T* x, const T* y, int L, int lane) {
+    T s0 = 0, s1 = 0;
     int i = lane;
     for (; i + 32 < L; i += 64) {
         s0 = fma(x[i], y[i], s0);
@@ -107,49 +114,85 @@ __device__ __forceinline__ double row_dot(const double* x, const double* y, int 
     return warp_sum(s0 + s1);
 }
 
+template <typename T>
 struct Ctx {
-    double* rows;     // [2b][rowlen] in shared memory
-    double* nrm;      // [2b]
+    T* rows;          // [2b][rowlen] in shared memory
+    T* nrm;           // [2b]
     int* rid;         // [2b] global row index or -1
     int rowlen, L;    // row length in smem (W part + Z part), W part length
-    double floor2, tol;
+    T floor2, tol2;
 };
 
+// Rotation parameters (cs, sn, t) zeroing <w_p, w_q> = g for |w_p|^2 = a,
+// |w_q|^2 = b.  FP64: t is found in FP32 (an inexact angle only slows the
+// last digits of convergence), cs = 1/sqrt(1+t^2) is then refined by two
+// Newton steps in FP64 so that cs^2 + sn^2 = 1 to FP64 rounding: the rotation
+// applied to the rows is orthogonal in FP64.  FP32: computed directly.
+__device__ __forceinline__ void rot_params(double a, double b, double g, double& cs, double& sn, double& t) {
+    const double r = b - a;
+    // scale (r, g) by a power of two so that both fit FP32's range
+    const double m = fmax(fabs(r), fabs(g));
+    int e = (int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023;
+    e = e < -1022 ? -1022 : (e > 1022 ? 1022 : e);
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);
+    const float rf = (float)(r * sc), gf = (float)(g * sc);
+    const float zeta = rf / (2.0f * gf);
+    float tf;
+    if (fabsf(zeta) > 1e18f)
+        tf = 0.5f / zeta;
+    else
+        tf = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+    t = (double)tf;
+    const double q = fma(t, t, 1.0);
+    double c = (double)rsqrtf((float)q);
+    c = c * fma(-0.5 * q, c * c, 1.5);
+    c = c * fma(-0.5 * q, c * c, 1.5);
+    cs = c;
+    sn = c * t;
+}
+
+__device__ __forceinline__ void rot_params(float a, float b, float g, float& cs, float& sn, float& t) {
+    const float zeta = (b - a) / (2.0f * g);
+    t = fabsf(zeta) > 1e18f ? 0.5f / zeta : copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+    cs = rsqrtf(fmaf(t, t, 1.0f));
+    sn = cs * t;
+}
+
 // One warp: rows p, q (shared-memory slots).  Returns 1 if it rotated.
-__device__ int pair_rotate(const Ctx& C, int p, int q, int lane) {
+template <typename T>
+__device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     if (C.rid[p] < 0 || C.rid[q] < 0) return 0;
-    double* rp = C.rows + (size_t)p * C.rowlen;
-    double* rq = C.rows + (size_t)q * C.rowlen;
-    const double a = C.nrm[p], b = C.nrm[q];
+    T* rp = C.rows + (size_t)p * C.rowlen;
+    T* rq = C.rows + (size_t)q * C.rowlen;
+    const T a = C.nrm[p], b = C.nrm[q];
     if (a <= C.floor2 || b <= C.floor2) {
-        if (a <= C.floor2 && a != 0.0) {
-            for (int i = lane; i < C.L; i += 32) rp[i] = 0.0;
+        if (a <= C.floor2 && a != T(0)) {
+            for (int i = lane; i < C.L; i += 32) rp[i] = T(0);
             __syncwarp();
-            if (lane == 0) C.nrm[p] = 0.0;
+            if (lane == 0) C.nrm[p] = T(0);
         }
-        if (b <= C.floor2 && b != 0.0) {
-            for (int i = lane; i < C.L; i += 32) rq[i] = 0.0;
+        if (b <= C.floor2 && b != T(0)) {
+            for (int i = lane; i < C.L; i += 32) rq[i] = T(0);
             __syncwarp();
-            if (lane == 0) C.nrm[q] = 0.0;
+            if (lane == 0) C.nrm[q] = T(0);
         }
         __syncwarp();
         return 0;
     }
-    const double g = row_dot(rp, rq, C.L, lane);
-    if (g == 0.0 || fabs(g) <= C.tol * sqrt(a) * sqrt(b)) return 0;
-    const double zeta = (b - a) / (2.0 * g);
-    const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-    const double cs = 1.0 / sqrt(1.0 + t * t);
-    const double sn = cs * t;
+    const T g = row_dot(rp, rq, C.L, lane);
+    if (g == T(0) || g * g <= C.tol2 * a * b) return 0;
+    T cs, sn, t;
+    rot_params(a, b, g, cs, sn, t);
+    if (t == T(0)) return 0;
     for (int i = lane; i < C.rowlen; i += 32) {
-        const double x = rp[i], y = rq[i];
+        const T x = rp[i], y = rq[i];
         rp[i] = fma(cs, x, -sn * y);
         rq[i] = fma(sn, x, cs * y);
     }
     __syncwarp();
-    double na = a - t * g, nb = b + t * g;
-    if (na < 0.1 * a) na = row_dot(rp, rp, C.L, lane);
-    if (nb < 0.1 * b) nb = row_dot(rq, rq, C.L, lane);
+    T na = fma(-t, g, a), nb = fma(t, g, b);
+    if (na < T(0.1) * a) na = row_dot(rp, rp, C.L, lane);
+    if (nb < T(0.1) * b) nb = row_dot(rq, rq, C.L, lane);
     if (lane == 0) {
         C.nrm[p] = na;
         C.nrm[q] = nb;
@@ -158,9 +201,10 @@ __device__ int pair_rotate(const Ctx& C, int p, int q, int lane) {
     return 1;
 }
 
-// All pairs inside slots [base, base+b) of one block (circle method), for
-// both blocks at once; then all cross pairs between the two blocks.
-__device__ int process_block_pair(const Ctx& C, int b, bool intra, int warp, int lane) {
+// All pairs inside each of the two blocks (circle method, first round of a
+// sweep only), then all cross pairs between the two blocks.
+template <typename T>
+__device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, int lane) {
     int rot = 0;
     if (intra && b > 1) {
         const int bp = b + (b & 1);
@@ -182,35 +226,50 @@ __device__ int process_block_pair(const Ctx& C, int b, bool intra, int warp, int
     return rot;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
                                                        double tol_in, unsigned long long timeout_ns, int ld) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool kF32 = sizeof(T) == 4;
     const int op = cta_op[blockIdx.x];
     const int g = cta_rank[blockIdx.x];
     const int G = group[op];
     const OpDesc& d = descs[op];
     unsigned* sw = sync + (size_t)op * kSyncWords;
-    const int c = d.c, L = d.L, b = d.jb;
-    double* W = d.W;
-    double* Z = d.transposed ? d.Z : nullptr;
+    const int c = d.c, L = d.L;
+    const int b = kF32 ? d.jb32 : d.jb;
+    T* W;
+    T* Z;
+    if constexpr (kF32) {
+        W = d.W32;
+        Z = d.U32;
+    } else {
+        W = d.W;
+        Z = d.transposed ? d.Z : nullptr;
+    }
     const int zl = Z ? c : 0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned gen = 0;
-    __shared__ double s_floor2;
+    __shared__ double s_floor2, s_scale;
     __shared__ int s_conv;
 
-    Ctx C;
+    Ctx<T> C;
     C.rowlen = L + zl;
     C.L = L;
-    C.rows = reinterpret_cast<double*>(smem_raw);
+    C.rows = reinterpret_cast<T*>(smem_raw);
     C.nrm = C.rows + (size_t)2 * b * C.rowlen;
     C.rid = reinterpret_cast<int*>(C.nrm + 2 * b);
-    C.tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * DBL_EPSILON;
+    {
+        const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
+        const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
+        C.tol2 = (T)(tol * tol);
+    }
 
-    // Z = I and the squared row norms (for the zero floor)
+    // squared row norms of the FP64 input (for the zero floor and the FP32 scale)
+    const double* W64 = kF32 ? d.W0 : d.W;
     for (int row = g * JW + warp; row < c; row += G * JW) {
-        const double* w = W + (size_t)row * ld;
+        const double* w = W64 + (size_t)row * ld;
         double a = 0.0;
         for (int i = lane; i < L; i += 32) {
             const double x = __ldcg(w + i);
@@ -218,17 +277,35 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         }
         a = warp_sum(a);
         if (lane == 0) __stcg(d.snorm + row, a);
-        if (Z)
-            for (int i = lane; i < c; i += 32) __stcg(Z + (size_t)row * ld + i, i == row ? 1.0 : 0.0);
     }
     if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
     if (threadIdx.x == 0) {
         double f = 0.0;
         for (int j = 0; j < c; ++j) f += __ldcg(d.snorm + j);
-        s_floor2 = DBL_EPSILON * DBL_EPSILON * f;
+        s_floor2 = (kF32 ? (double)FLT_EPSILON * FLT_EPSILON : DBL_EPSILON * DBL_EPSILON) * f;
+        s_scale = f > 0.0 ? sqrt((double)c / f) : 1.0;   // FP32 pass: rows of unit mean square norm
     }
     __syncthreads();
-    C.floor2 = s_floor2;
+    // initial Z (identity, or Zinit) and, for the FP32 pass, the scaled copy of the rows
+    for (int row = g * JW + warp; row < c; row += G * JW) {
+        if (Z) {
+            bool copied = false;
+            if constexpr (!kF32) {
+                if (d.Zinit) {
+                    for (int i = lane; i < c; i += 32) __stcg(Z + (size_t)row * ld + i, __ldcg(d.Zinit + (size_t)row * ld + i));
+                    copied = true;
+                }
+            }
+            if (!copied)
+                for (int i = lane; i < c; i += 32) Z[(size_t)row * ld + i] = (i == row) ? T(1) : T(0);
+        }
+        if constexpr (kF32) {
+            const double sc = s_scale;
+            for (int i = lane; i < L; i += 32) W[(size_t)row * ld + i] = (float)(__ldcg(d.W0 + (size_t)row * ld + i) * sc);
+        }
+    }
+    C.floor2 = (T)(kF32 ? s_floor2 * s_scale * s_scale : s_floor2);
+    if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
     {
         const int nb = (c + b - 1) / b;
         const int nbp = nb + (nb & 1);
@@ -247,24 +324,24 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                         const int blk = bl[s / b];
                         const int row = blk * b + (s % b);
                         const bool ok = blk < nb && row < c;
-                        double* dst = C.rows + (size_t)s * C.rowlen;
+                        T* dst = C.rows + (size_t)s * C.rowlen;
                         if (ok) {
-                            const double* w = W + (size_t)row * ld;
+                            const T* w = W + (size_t)row * ld;
                             for (int k = lane; k < L; k += 32) dst[k] = __ldcg(w + k);
                             if (Z)
                                 for (int k = lane; k < c; k += 32) dst[L + k] = __ldcg(Z + (size_t)row * ld + k);
                             __syncwarp();
-                            double nv;
+                            T nv;
                             if (r == 0)
                                 nv = row_dot(dst, dst, L, lane);   // fresh norms at the start of a sweep
                             else
-                                nv = __ldcg(d.snorm + row);
+                                nv = (T)__ldcg(d.snorm + row);
                             if (lane == 0) {
                                 C.nrm[s] = nv;
                                 C.rid[s] = row;
                             }
                         } else if (lane == 0) {
-                            C.nrm[s] = 0.0;
+                            C.nrm[s] = T(0);
                             C.rid[s] = -1;
                         }
                     }
@@ -274,12 +351,12 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                     for (int s = warp; s < 2 * b; s += JW) {
                         const int row = C.rid[s];
                         if (row < 0) continue;
-                        const double* src = C.rows + (size_t)s * C.rowlen;
-                        double* w = W + (size_t)row * ld;
+                        const T* src = C.rows + (size_t)s * C.rowlen;
+                        T* w = W + (size_t)row * ld;
                         for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
                         if (Z)
                             for (int k = lane; k < c; k += 32) __stcg(Z + (size_t)row * ld + k, src[L + k]);
-                        if (lane == 0) __stcg(d.snorm + row, C.nrm[s]);
+                        if (lane == 0) __stcg(d.snorm + row, (double)C.nrm[s]);
                     }
                     __syncthreads();
                 }
@@ -292,8 +369,12 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
             used = sweep + 1;
         }
         if (g == 0 && threadIdx.x == 0) {
-            if (d.sweeps_out) *d.sweeps_out = used;
-            if (!conv) atomicOr(d.status, (int)MPDO_ST_NOCONV);
+            if (!kF32) {
+                if (d.sweeps_out) *d.sweeps_out += used;
+                if (!conv) atomicOr(d.status, (int)MPDO_ST_NOCONV);
+            } else if (d.sweeps_out) {
+                *d.sweeps_out += used << 16;   // FP32 sweeps in the high half
+            }
         }
     }
     return;
@@ -306,9 +387,9 @@ timeout:
 int jacobi_threads() { return JT; }
 size_t jacobi_sync_words_per_op() { return kSyncWords; }
 
-int jacobi_block_rows(int rowlen, int c) {
+int jacobi_block_rows(int rowlen, int c, int elem_bytes) {
     int b = kMaxB;
-    while (b > 1 && (size_t)2 * b * rowlen * sizeof(double) > (size_t)kRowBytes) b >>= 1;
+    while (b > 1 && (size_t)2 * b * rowlen * elem_bytes > (size_t)kRowBytes) b >>= 1;
     while (b > 1 && b >= c) b >>= 1;   // at least two blocks when c > 1
     return b;
 }
@@ -319,27 +400,34 @@ int jacobi_pairs_per_round(int c, int b) {
 }
 
 cudaError_t jacobi_max_resident(int* blocks) {
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per64 = 0, per32 = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, JT, kSmemBytes);
-    if (e != cudaSuccess) return e;
-    *blocks = sms * per_sm;
+    if ((e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, jacobi_kernel<double>, JT, kSmemBytes)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, jacobi_kernel<float>, JT, kSmemBytes)) != cudaSuccess)
+        return e;
+    *blocks = sms * (per64 < per32 ? per64 : per32);
     return cudaSuccess;
 }
 
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, cudaStream_t st) {
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st) {
     (void)nops;
     if (grid <= 0) return cudaSuccess;
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
                     (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
-    return cudaLaunchCooperativeKernel((const void*)jacobi_kernel, dim3(grid), dim3(JT), args, kSmemBytes, st);
+    const void* fn = fp32 ? (const void*)jacobi_kernel<float> : (const void*)jacobi_kernel<double>;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(JT), args, kSmemBytes, st);
 }
 
 }  // namespace mpdo

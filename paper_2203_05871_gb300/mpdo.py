@@ -80,7 +80,7 @@ def load_library(path: str = LIB_PATH):
         "mpdo_profile_read": (ctypes.c_int, [vp, _dp, ctypes.POINTER(ctypes.c_longlong), _dp, ctypes.c_int,
                                              ctypes.c_int]),
         "mpdo_profile_sweeps": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong),
-                                               ctypes.POINTER(ctypes.c_longlong)]),
+                                               ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_last_error": (ctypes.c_char_p, []),
@@ -102,7 +102,8 @@ def exported_symbols() -> list[str]:
             "mpdo_last_error", "mpdo_destroy"]
 
 
-PROFILE_KINDS = ["merge_gate", "jacobi_svd", "truncate", "reconstruct", "trace", "measure", "build_gates"]
+PROFILE_KINDS = ["merge_gate", "jacobi_svd", "truncate", "reconstruct", "trace", "measure", "build_gates",
+                 "jacobi_fp32", "precond_gemm"]
 
 
 def schedule(n: int, bonds):
@@ -286,8 +287,8 @@ class Solver:
         _check(self._lib.mpdo_profile_enable(self._h, int(on)))
 
     def profile_read(self, reset: bool = False):
-        sw, sv = ctypes.c_longlong(), ctypes.c_longlong()
-        _check(self._lib.mpdo_profile_sweeps(self._h, ctypes.byref(sw), ctypes.byref(sv)))
+        sw, sv, s32 = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.mpdo_profile_sweeps(self._h, ctypes.byref(sw), ctypes.byref(sv), ctypes.byref(s32)))
         K = len(PROFILE_KINDS)
         ms = np.zeros(K)
         ln = np.zeros(K, np.int64)
@@ -298,6 +299,7 @@ class Solver:
                for i, k in enumerate(PROFILE_KINDS)}
         out["jacobi_svd"]["sweeps"] = int(sw.value)
         out["jacobi_svd"]["svds"] = int(sv.value)
+        out["jacobi_svd"]["sweeps_fp32"] = int(s32.value)
         return out
 
     def rank_log(self, n_steps: int):

@@ -13,6 +13,7 @@ from oracle import dense, model, schedule, tebd
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
+TOL_MIXED = 1e-5     # mixed-precision path (FP32-preconditioned SVD) vs the FP64 oracle
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -191,6 +192,54 @@ def test_chi256_one_step_sampled():
     pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
     g = s.measure_2q(pairs, "ZZ", connected=True)[0]
     assert np.abs(g - o.zz_connected(pairs)).max() <= TOL
+
+
+# ---------------------------------------------------------------------------
+# mixed-precision path: FP32 preconditioning Jacobi + FP64 finishing sweeps
+# ---------------------------------------------------------------------------
+def _mixed():
+    from paper_2203_05871_gb300 import MIXED_TF32
+    return MIXED_TF32
+
+
+def test_mixed_chain8_forty_steps():
+    wl = W.chain8_fp64()
+    s = solver_for(wl, precision=_mixed())
+    worst = compare_to_oracle(wl, wl.steps, s, tol=TOL_MIXED)
+    assert worst <= TOL_MIXED
+
+
+@pytest.mark.parametrize("bonds,n", [(W.ring_bonds(8), 8), (W.grid_snake_bonds(3, 3), 9)])
+def test_mixed_swap_routed(bonds, n):
+    wl = W.random_model(n, bonds, 57, chi_max=32, cutoff=1e-11, dt=0.05)
+    s = solver_for(wl, precision=_mixed())
+    compare_to_oracle(wl, 3, s, tol=TOL_MIXED)
+
+
+def test_mixed_batched_uneven_chi():
+    wl = W.random_model(8, W.chain_bonds(8), 63, batch=3, chi_max=32, cutoff=1e-11)
+    wl.chi_max[:] = [8, 16, 32]
+    s = solver_for(wl, chi_cap=32, precision=_mixed())
+    compare_to_oracle(wl, 4, s, tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("decay", [0.0, 0.045])
+def test_mixed_chi256_one_step_sampled(decay):
+    n = 10
+    wl = W.uniform_model("chain10_chi256", n, W.chain_bonds(n), chi_max=256, cutoff=1e-10, dt=0.02)
+    dims, tens = W.random_mpo_state(n, 256, seed=11, decay=decay)
+    s = solver_for(wl, chi_cap=256, precision=_mixed())
+    s.set_state(0, dims, tens)
+    s.step(1)
+    log = [int(k) for k in s.rank_log(1)[0]]
+    st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
+    o = tebd.TEBD(wl, 0, state=st)
+    o.run(1, forced_k=log)
+    gz = s.measure_1q(range(n), "Z")[0]
+    assert np.abs(gz - o.z()).max() <= TOL_MIXED
+    pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
+    g = s.measure_2q(pairs, "ZZ", connected=True)[0]
+    assert np.abs(g - o.zz_connected(pairs)).max() <= TOL_MIXED
 
 
 def test_errors_are_codes_not_crashes():

@@ -228,11 +228,14 @@ def random_model(n: int, bonds: List[Bond], seed: int, *, batch: int = 1, chi_ma
                     int(steps), init)
 
 
-def random_mpo_state(n: int, chi: int, seed: int):
+def random_mpo_state(n: int, chi: int, seed: int, decay: float = 0.0):
     """Seeded random MPO site tensors B[p] of shape (chi_l, 4, chi_r) with the
     bond dimensions capped by 4^min(p+1, n-p-1) (the exact-representation
-    bound of App. B) and entries N(0,1)/sqrt(4 chi_l).  Used to start a
-    benchmark at saturated bond dimension.  Returns (dims, tensors)."""
+    bound of App. B) and entries N(0,1)/sqrt(4 chi_l) * exp(-decay * r) on
+    right-bond index r.  decay = 0 gives a flat (worst-case) Schmidt spectrum;
+    decay > 0 grades the bonds the way time-evolved states are graded (their
+    Schmidt values fall off).  Used to start a benchmark at saturated bond
+    dimension.  Returns (dims, tensors)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     dims = [1]
     for p in range(n - 1):
@@ -241,7 +244,8 @@ def random_mpo_state(n: int, chi: int, seed: int):
     tensors = []
     for p in range(n):
         cl, cr = dims[p], dims[p + 1]
-        tensors.append(rng.standard_normal((cl, 4, cr)) / np.sqrt(4.0 * cl))
+        scale = np.exp(-decay * np.arange(cr)) if decay > 0 else np.ones(cr)
+        tensors.append(rng.standard_normal((cl, 4, cr)) / np.sqrt(4.0 * cl) * scale[None, None, :])
     return dims, tensors
 
 
