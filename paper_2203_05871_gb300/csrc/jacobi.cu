@@ -102,16 +102,22 @@ __device__ __forceinline__ int tour_player(int x, int step, int cp) {
     return x == 0 ? 0 : 1 + ((x - 1 + step) % (cp - 1));
 }
 
+// <x, y> over L elements: lane-strided with four independent accumulators
+// (shared-memory latency is hidden by ILP: one CTA of 8 warps per SM)
 template <typename T>
 __device__ __forceinline__ T row_dot(const T* x, const T* y, int L, int lane) {
-    T s0 = 0, s1 = 0;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     int i = lane;
-    for (; i + 32 < L; i += 64) {
-        s0 = fma(x[i], y[i], s0);
-        s1 = fma(x[i + 32], y[i + 32], s1);
+    for (; i + 96 < L; i += 128) {
+        const T x0 = x[i], x1 = x[i + 32], x2 = x[i + 64], x3 = x[i + 96];
+        const T y0 = y[i], y1 = y[i + 32], y2 = y[i + 64], y3 = y[i + 96];
+        s0 = fma(x0, y0, s0);
+        s1 = fma(x1, y1, s1);
+        s2 = fma(x2, y2, s2);
+        s3 = fma(x3, y3, s3);
     }
-    if (i < L) s0 = fma(x[i], y[i], s0);
-    return warp_sum(s0 + s1);
+    for (; i < L; i += 32) s0 = fma(x[i], y[i], s0);
+    return warp_sum((s0 + s1) + (s2 + s3));
 }
 
 template <typename T>
@@ -184,7 +190,21 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
-    for (int i = lane; i < C.rowlen; i += 32) {
+    int i = lane;
+    for (; i + 96 < C.rowlen; i += 128) {
+        T x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = rp[i + 32 * u];
+            y[u] = rq[i + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            rp[i + 32 * u] = fma(cs, x[u], -sn * y[u]);
+            rq[i + 32 * u] = fma(sn, x[u], cs * y[u]);
+        }
+    }
+    for (; i < C.rowlen; i += 32) {
         const T x = rp[i], y = rq[i];
         rp[i] = fma(cs, x, -sn * y);
         rq[i] = fma(sn, x, cs * y);
