@@ -70,7 +70,7 @@ typedef struct {
     int storage;             /* MPDO_STORE_F64 | MPDO_STORE_F32 */
     int trotter_order;       /* 2 (symmetric second-order product) */
     int force_trace;         /* 1: rho /= tr rho after every step (App. B b_force_rho_trace) */
-    int jacobi_max_sweeps;   /* sweep limit of the Jacobi SVD (default 40) */
+    int jacobi_max_sweeps;   /* sweep limit of the Jacobi SVD (default 100, at most 128) */
     double jacobi_tol;       /* <= 0: sqrt(L) * DBL_EPSILON for rows of length L */
     unsigned barrier_timeout_ms;  /* limit of every device-side wait (default 4000) */
     int max_slots;           /* <= 0: automatic; else max two-site ops in flight */

@@ -46,7 +46,7 @@ def _load():
 
 
 def jacobi_rows(W: np.ndarray, Z: np.ndarray | None = None, tol: float | None = None,
-                max_sweeps: int = 60) -> int:
+                max_sweeps: int = 200) -> int:
     """Rotate the rows of W (and Z) in place until mutually orthogonal."""
     assert W.dtype == np.float64 and W.flags.c_contiguous
     c, L = W.shape

@@ -482,7 +482,7 @@ int mpdo_config_default(mpdo_config* cfg) {
     cfg->storage = MPDO_STORE_F64;
     cfg->trotter_order = 2;
     cfg->force_trace = 1;
-    cfg->jacobi_max_sweeps = 40;
+    cfg->jacobi_max_sweeps = 100;
     cfg->jacobi_tol = 0.0;
     cfg->barrier_timeout_ms = 4000;
     cfg->max_slots = 0;

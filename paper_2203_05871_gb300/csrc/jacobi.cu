@@ -24,7 +24,11 @@
 // cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q,
 // and then |w_p|^2 = a - t g, |w_q|^2 = b + t g (recomputed from the row when
 // the update loses more than 90% of the old value, and at every sweep start).
-// A pair is skipped when g^2 <= tol^2 a b (tol = sqrt(L) eps unless set).
+// A pair is skipped when |g| <= tol max(a, b) (tol = sqrt(L) eps unless set):
+// the rotation would then move either row by less than tol relative to the
+// larger one, i.e. below the normwise accuracy of the SVD.  Pairs whose rows
+// both lie in the discarded tail of the spectrum are skipped as well (see
+// tail_threshold).
 //
 // The same kernel, instantiated for float, is the preconditioning pass of the
 // mixed-precision SVD: it orthogonalises an FP32 copy of the rows (scaled to
@@ -126,7 +130,8 @@ struct Ctx {
     T* nrm;           // [2b]
     int* rid;         // [2b] global row index or -1
     int rowlen, L;    // row length in smem (W part + Z part), W part length
-    T floor2, tol2;
+    T floor2, tol;
+    T tau;            // tail threshold of this sweep: pairs of rows both below it are skipped
 };
 
 // Rotation parameters (cs, sn, t) zeroing <w_p, w_q> = g for |w_p|^2 = a,
@@ -164,6 +169,62 @@ __device__ __forceinline__ void rot_params(float a, float b, float g, float& cs,
     sn = cs * t;
 }
 
+// Tail threshold of a sweep.  With the squared row norms sorted ascending,
+// the tail is the longest run of smallest rows whose total weight is at most
+// min(cutoff/2 * total, 1/4 * a_ref), a_ref = the k_max-th largest squared
+// norm (k_max = min(chi_max, c)), leaving at least k_max rows outside it.
+// Pairs of tail rows are not rotated: the truncation discards them whatever
+// their mutual angles (their summed weight is below the cutoff), the kept
+// rows are still made orthogonal to them, and their largest singular value
+// (<= their Frobenius norm < sqrt(a_ref)/2) cannot reach the kept spectrum.
+// Returns -1 (no tail) when cutoff is 0.  All threads of the CTA call it;
+// buf is >= 2 * next_pow2(c) doubles of shared memory.
+__device__ double tail_threshold(const OpDesc& d, int c, double* buf) {
+    __shared__ double s_tau;
+    int n2 = 1;
+    while (n2 < c) n2 <<= 1;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) buf[i] = i < c ? __ldcg(d.snorm + i) : INFINITY;
+    __syncthreads();
+    // bitonic sort, ascending
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const double x = buf[i], y = buf[l];
+                    if ((x > y) == up) {
+                        buf[i] = y;
+                        buf[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) {
+        double tau = -1.0;
+        const int kmax = d.chi_max < c ? d.chi_max : c;
+        if (d.cutoff > 0.0 && kmax < c) {
+            double total = 0.0;
+            for (int i = 0; i < c; ++i) total += buf[i];
+            const double aref = buf[c - kmax];
+            const double budget = fmin(0.5 * d.cutoff * total, 0.25 * aref);
+            double acc = 0.0;
+            for (int i = 0; i < c - kmax; ++i) {
+                acc += buf[i];
+                if (acc > budget) break;
+                tau = buf[i];
+            }
+        }
+        s_tau = tau;
+    }
+    __syncthreads();
+    const double t = s_tau;
+    __syncthreads();
+    return t;
+}
+
 // One warp: rows p, q (shared-memory slots).  Returns 1 if it rotated.
 template <typename T>
 __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
@@ -185,8 +246,9 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         __syncwarp();
         return 0;
     }
+    if (a <= C.tau && b <= C.tau) return 0;      // both in the discarded tail
     const T g = row_dot(rp, rq, C.L, lane);
-    if (g == T(0) || g * g <= C.tol2 * a * b) return 0;
+    if (g == T(0) || fabs(g) <= C.tol * fmax(a, b)) return 0;
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
@@ -283,7 +345,8 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     {
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
         const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
-        C.tol2 = (T)(tol * tol);
+        C.tol = (T)tol;
+        C.tau = T(-1);
     }
 
     // squared row norms of the FP64 input (for the zero floor and the FP32 scale)
@@ -335,6 +398,19 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         int used = 0;
         for (int sweep = 0; sweep < sweeps && !conv; ++sweep) {
             int rot = 0;
+            // fresh squared row norms, then the tail threshold (same in every CTA)
+            for (int row = g * JW + warp; row < c; row += G * JW) {
+                const T* w = W + (size_t)row * ld;
+                T a = 0;
+                for (int i = lane; i < L; i += 32) {
+                    const T x = __ldcg(w + i);
+                    a = fma(x, x, a);
+                }
+                a = warp_sum(a);
+                if (lane == 0) __stcg(d.snorm + row, (double)a);
+            }
+            if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
+            C.tau = (T)tail_threshold(d, c, reinterpret_cast<double*>(smem_raw));
             for (int r = 0; r < nbp - 1; ++r) {
                 for (int i = g; i < npair; i += G) {
                     const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
@@ -351,11 +427,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                             if (Z)
                                 for (int k = lane; k < c; k += 32) dst[L + k] = __ldcg(Z + (size_t)row * ld + k);
                             __syncwarp();
-                            T nv;
-                            if (r == 0)
-                                nv = row_dot(dst, dst, L, lane);   // fresh norms at the start of a sweep
-                            else
-                                nv = (T)__ldcg(d.snorm + row);
+                            const T nv = (T)__ldcg(d.snorm + row);
                             if (lane == 0) {
                                 C.nrm[s] = nv;
                                 C.rid[s] = row;

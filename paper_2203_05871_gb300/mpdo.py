@@ -145,7 +145,7 @@ class Solver:
     """One libmpdo context: B instances of an N-qubit model on one GPU."""
 
     def __init__(self, n_qubits: int, batch: int = 1, chi_cap: int = 32, precision: int = FP64,
-                 storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 40,
+                 storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 100,
                  jacobi_tol: float = 0.0, barrier_timeout_ms: int = 4000, max_slots: int = 0,
                  device: Optional[int] = None):
         lib = load_library()
