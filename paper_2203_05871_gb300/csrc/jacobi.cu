@@ -24,11 +24,12 @@
 // cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q,
 // and then |w_p|^2 = a - t g, |w_q|^2 = b + t g (recomputed from the row when
 // the update loses more than 90% of the old value, and at every sweep start).
-// A pair is skipped when |g| <= tol max(a, b) (tol = sqrt(L) eps unless set):
-// the rotation would then move either row by less than tol relative to the
-// larger one, i.e. below the normwise accuracy of the SVD.  Pairs whose rows
-// both lie in the discarded tail of the spectrum are skipped as well (see
-// tail_threshold).
+// A pair is skipped when g^2 <= tol^2 a b (tol = sqrt(L) eps unless set): kept
+// rows are normalised into singular vectors, so they must be orthogonal
+// relative to their own norms.  Pairs whose rows both lie in the discarded
+// tail of the spectrum are skipped (see tail_threshold), and a pair of one
+// tail row with one other row only needs |g| <= tol max(a, b): the rotation
+// would move the larger row by less than tol of its norm.
 //
 // The same kernel, instantiated for float, is the preconditioning pass of the
 // mixed-precision SVD: it orthogonalises an FP32 copy of the rows (scaled to
@@ -246,9 +247,17 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         __syncwarp();
         return 0;
     }
-    if (a <= C.tau && b <= C.tau) return 0;      // both in the discarded tail
+    const bool ta = a <= C.tau, tb = b <= C.tau;
+    if (ta && tb) return 0;      // both in the discarded tail
     const T g = row_dot(rp, rq, C.L, lane);
-    if (g == T(0) || fabs(g) <= C.tol * fmax(a, b)) return 0;
+    if (g == T(0)) return 0;
+    if (ta || tb) {
+        // kept-side row vs tail row: normwise criterion (the rotation would move
+        // the larger row by less than tol of its norm)
+        if (fabs(g) <= C.tol * fmax(a, b)) return 0;
+    } else if (g * g <= C.tol * C.tol * a * b) {
+        return 0;                // relative criterion: rows that may be kept are normalised later
+    }
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
