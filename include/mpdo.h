@@ -108,7 +108,8 @@ int mpdo_build_gates(mpdo_ctx *ctx, const mpdo_model *model, double dt);
 
 /* Advance every instance by n_steps second-order Trotter steps.  Per op:
  * merge the two sites, apply the gate, weight by the left Schmidt values,
- * SVD (FP64 one-sided Jacobi), truncate, write the two new sites.  After each
+ * Householder QR (only R is kept), SVD of R (FP64 one-sided Jacobi on its
+ * rows), truncate, write the two new sites.  After each
  * step the trace is forced to 1 when cfg.force_trace.  Returns ENOCONV /
  * ENONFINITE / ETIMEOUT when some instance reported that status (the other
  * instances are still advanced), ESTATE before mpdo_build_gates. */
@@ -165,7 +166,7 @@ int mpdo_schedule(int n, int n_bonds, const int *bond_i, const int *bond_j, int 
  * of the step with CUDA events on the context stream and accumulates, per
  * kernel kind k (0 merge+gate, 1 Jacobi SVD (FP64), 2 truncate, 3 reconstruct,
  * 4 trace, 5 environments/measure, 6 gate build, 7 FP32 preconditioning
- * Jacobi, 8 preconditioner GEMMs), the device time in ms,
+ * Jacobi, 8 preconditioner GEMMs, 9 Householder QR), the device time in ms,
  * the number of launches and the algorithmic flops of the work launched
  * (merge 32 cl cm cr, gate 512 cl cr, SVD 21 n^3 with n = 4 max(cl, cr),
  * reconstruct 32 cl cr k; 0 for the other kinds).  mpdo_profile_read copies

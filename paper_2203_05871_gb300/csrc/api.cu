@@ -24,9 +24,9 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace mpdo
 
 namespace {
-constexpr int kProfKinds = 9;
+constexpr int kProfKinds = 10;
 enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6, K_JACOBI32 = 7,
-       K_GEMM = 8 };
+       K_GEMM = 8, K_QR = 9 };
 
 int fail(int code, const std::string& msg) {
     g_err = msg;
@@ -97,6 +97,7 @@ struct mpdo_ctx {
     int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]
     unsigned* d_sync = nullptr;
     int jacobi_resident = 0;
+    int qr_resident = 0;
     // measurement
     double *d_envL = nullptr, *d_envR = nullptr, *d_full = nullptr, *d_one_a = nullptr, *d_one_b = nullptr,
            *d_out = nullptr;
@@ -176,11 +177,11 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_sweeps, (size_t)s));
     c->h_sweeps.assign(s, 0);
     CU(dalloc(&c->d_desc, (size_t)s));
-    const int gcap = std::max(c->jacobi_resident, s);
-    CU(dalloc(&c->d_cta, (size_t)2 * (2 * gcap + s)));
+    const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), s);
+    CU(dalloc(&c->d_cta, (size_t)3 * (2 * gcap + s)));
     CU(dalloc(&c->d_sync, (size_t)s * jacobi_sync_words_per_op()));
     CU(cudaMallocHost((void**)&c->h_desc, sizeof(OpDesc) * s));
-    CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * 2 * (2 * gcap + s)));
+    CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * 3 * (2 * gcap + s)));
     if (c->mixed) {
         CU(dalloc(&c->d_W0, (size_t)s * mat));
         CU(dalloc(&c->d_E, (size_t)s * mat));
@@ -237,7 +238,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     const int nops = (int)items.size();
     const int N = c->N, cap = c->cap, ld = c->ld;
     const size_t mat = (size_t)ld * ld;
-    std::vector<double> work(nops);
+    std::vector<double> work(nops), qwork(nops);
     for (int s = 0; s < nops; ++s) {
         const Item& it = items[s];
         const Op& op = c->layers[it.layer][it.idx];
@@ -251,9 +252,9 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.cr = dm[p + 2];
         d.m = 4 * d.cl;
         d.n = 4 * d.cr;
-        d.transposed = d.m > d.n ? 1 : 0;
+        d.transposed = 0;                 // the QR step leaves min(m, n) rows of length n
         d.c = std::min(d.m, d.n);
-        d.L = std::max(d.m, d.n);
+        d.L = d.n;
         d.chi_max = c->chi_max[b];
         d.cutoff = c->cutoff[b];
         d.G = c->d_gates + ((size_t)b * c->n_ops + d.op) * 256;
@@ -263,14 +264,15 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.lam_out = c->d_lam + ((size_t)b * N + p) * cap;
         d.thetap = c->d_thetap + (size_t)s * mat;
         d.W = c->d_W + (size_t)s * mat;
-        d.Z = c->d_Z + (size_t)s * mat;
+        d.Z = nullptr;
+        d.Acm = c->d_Z + (size_t)s * mat;
         d.Yk = c->d_Yk + (size_t)s * cap * ld;
         d.snorm = c->d_snorm + (size_t)s * ld;
         d.k_out = c->d_dims + (size_t)b * (N + 1) + p + 1;
         d.status = c->d_status + b;
         d.max_disc = c->d_maxdisc + b;
         d.rank_log = nullptr;
-        d.jb = jacobi_block_rows(d.L + (d.transposed ? d.c : 0), d.c, 8);
+        d.jb = jacobi_block_rows(d.L, d.c, 8);
         d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
         d.sweeps_out = c->d_sweeps + s;
         d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
@@ -278,8 +280,9 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
         d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
         d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
-        d.Zinit = (c->mixed && d.transposed) ? d.Q : nullptr;
+        d.Zinit = nullptr;
         work[s] = (double)d.c * d.c * (double)d.L;
+        qwork[s] = (double)d.m * d.n * d.c;
     }
     CU(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
     double fl_merge = 0.0, fl_svd = 0.0;
@@ -294,7 +297,8 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     p_merge.stop();
 
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
-    const int gcap = std::max(c->jacobi_resident, c->slots);
+    const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), c->slots);
+    double qr_flops_chunk = 0.0;
     // Jacobi launch plan: share the co-resident CTAs among the ops in
     // proportion to their work; h_cta/d_cta hold [op of each CTA | rank | CTAs per op]
     auto plan = [&](bool fp32, int* hbase, int& total) -> int {
@@ -343,6 +347,49 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         return MPDO_OK;
     };
     CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, c->st));
+    // Householder QR of every theta~ (R's rows go to W0)
+    {
+        const int R = c->qr_resident;
+        const int QW = qr_threads() / 32;
+        double wsum = 0.0;
+        for (double w : qwork) wsum += w;
+        std::vector<int> G(nops, 1);
+        int total = 0;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            const int need = std::max(1, (d.n + QW - 1) / QW);
+            int g = (int)std::floor((double)R * qwork[s] / std::max(wsum, 1.0));
+            G[s] = std::max(1, std::min(need, g));
+            total += G[s];
+        }
+        while (total > R) {
+            int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
+            if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident QR CTAs");
+            G[arg]--;
+            total--;
+        }
+        int* hbase = c->h_cta + (size_t)2 * (2 * gcap + c->slots);
+        int* dbase = c->d_cta + (size_t)2 * (2 * gcap + c->slots);
+        int t = 0;
+        for (int s = 0; s < nops; ++s) {
+            hbase[2 * total + s] = G[s];
+            for (int g = 0; g < G[s]; ++g, ++t) {
+                hbase[t] = s;
+                hbase[total + t] = g;
+            }
+        }
+        double fl_qr = 0.0;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            fl_qr += 4.0 * d.m * d.n * d.c - 2.0 * (d.m + d.n) * d.c * d.c + 4.0 / 3.0 * d.c * d.c * d.c;
+        }
+        qr_flops_chunk = fl_qr;
+        CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
+        CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+        ProfScope p_qr(c, K_QR);
+        CU(launch_qr(c->d_desc, dbase, dbase + total, dbase + 2 * total, c->d_sync, total, timeout_ns, ld, c->st));
+        p_qr.stop();
+    }
     double fl_gemm = 0.0;
     if (c->mixed) {
         // FP32 preconditioning Jacobi on (W32 | U32)
@@ -402,6 +449,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         fl_rec += 32.0 * d.cl * d.cr * c->h_dims[(size_t)d.b * (N + 1) + c->layers[items[s].layer][items[s].idx].p + 1];
     }
     prof_collect(c, K_MERGE, fl_merge);
+    prof_collect(c, K_QR, qr_flops_chunk);
     prof_collect(c, K_JACOBI, fl_svd);
     if (c->mixed) {
         prof_collect(c, K_JACOBI32, 0.0);
@@ -541,6 +589,10 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
         fail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA,
              std::string("device allocation: ") + cudaGetErrorString(e));
         return bail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA);
+    }
+    if ((e = qr_max_resident(&c->qr_resident)) != cudaSuccess || c->qr_resident < 1) {
+        fail(MPDO_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));
+        return bail(MPDO_ECUDA);
     }
     if ((e = jacobi_max_resident(&c->jacobi_resident)) != cudaSuccess || c->jacobi_resident < 1) {
         fail(MPDO_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));

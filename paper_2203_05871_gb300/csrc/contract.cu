@@ -2,7 +2,8 @@
 //   merge + gate + weight:
 //     Theta [l,s1,s2,r] = sum_m A[l,s1,m] B[m,s2,r]
 //     Theta'[l,s1',s2',r] = sum_{s1,s2} G[s1's2', s1s2] Theta[l,s1,s2,r]
-//     theta~ = lambda_{p-1}[l] * Theta'   (rows (l,s1'), cols (s2',r))
+//     theta~ = lambda_{p-1}[l] * Theta'   (rows (l,s1'), cols (s2',r)), stored
+//     column-major for the QR step
 //   reconstruct:
 //     B_p'[(l,s1), j] = sum_c Theta'[(l,s1), c] Yk[j, c]
 // Site tensors are stored [chi_l][4][chi_cap] (row (l,s) of length chi_cap).
@@ -70,10 +71,7 @@ __global__ void __launch_bounds__(256) merge_gate_kernel(const OpDesc* descs, in
         const int s1 = o >> 2, s2 = o & 3;
         const int row = l * 4 + s1, col = s2 * d.cr + r;
         d.thetap[(size_t)row * ld + col] = v;
-        if (d.transposed)
-            d.W0[(size_t)col * ld + row] = lam * v;
-        else
-            d.W0[(size_t)row * ld + col] = lam * v;
+        d.Acm[(size_t)col * ld + row] = lam * v;
     }
 }
 

@@ -41,7 +41,7 @@ struct OpDesc {
     int op;            // op index within the step (for the rank log)
     int cl, cm, cr;    // bond dims chi_{p-1}, chi_p, chi_{p+1}
     int m, n;          // 4*cl, 4*cr
-    int transposed;    // 1: Jacobi rows are the columns of theta~ (m > n), with Z
+    int transposed;    // 1: Jacobi rows carry a c x c accumulator Z (unused since the QR step)
     int c, L;          // Jacobi problem: c rows of length L
     int jb;            // Jacobi block size (rows per shared-memory block), FP64 pass
     int jb32;          // same for the FP32 preconditioning pass
@@ -53,7 +53,8 @@ struct OpDesc {
     const double* lam_left;  // lambda_{p-1} (nullptr => 1)
     double* lam_out;   // lambda_p
     double* thetap;    // Theta'  m x n (ld)
-    double* W0;        // where merge writes theta~ (== W in the FP64 path)
+    double* Acm;       // theta~ column-major (column k at Acm + k*ld), input of the QR
+    double* W0;        // rows of R from the QR (== W in the FP64 path)
     double* W;         // Jacobi rows: theta~ (m x n) or theta~^T (n x m)
     double* Z;         // c x c rotation accumulator when transposed
     const double* Zinit;  // initial Z (nullptr => identity)
@@ -105,6 +106,11 @@ cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, c
 size_t jacobi_sync_words_per_op();
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+
+int qr_threads();
+cudaError_t qr_max_resident(int* blocks);
+cudaError_t launch_qr(const OpDesc* d_desc, const int* d_cta_op, const int* d_cta_rank, const int* d_group,
+                      unsigned* d_sync, int grid, unsigned long long timeout_ns, int ld, cudaStream_t st);
 
 // C = alpha * A op(B) + beta * D (- I): see gemm.cu
 struct GemmDesc {

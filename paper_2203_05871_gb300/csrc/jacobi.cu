@@ -26,10 +26,7 @@
 // the update loses more than 90% of the old value, and at every sweep start).
 // A pair is skipped when g^2 <= tol^2 a b (tol = sqrt(L) eps unless set): kept
 // rows are normalised into singular vectors, so they must be orthogonal
-// relative to their own norms.  Pairs whose rows both lie in the discarded
-// tail of the spectrum are skipped (see tail_threshold), and a pair of one
-// tail row with one other row only needs |g| <= tol max(a, b): the rotation
-// would move the larger row by less than tol of its norm.
+// relative to their own norms.
 //
 // The same kernel, instantiated for float, is the preconditioning pass of the
 // mixed-precision SVD: it orthogonalises an FP32 copy of the rows (scaled to
@@ -40,6 +37,7 @@
 #include <float.h>
 #include <mpdo.h>
 
+#include "coop.cuh"
 #include "internal.h"
 
 namespace mpdo {
@@ -51,57 +49,6 @@ constexpr int JT = JW * 32;
 constexpr int kRowBytes = 128 * 1024;                  // two blocks of rows in shared memory
 constexpr int kMaxB = 32;
 constexpr int kSmemBytes = kRowBytes + 4 * kMaxB * 8;  // rows + norms (2b) + row ids
-constexpr int kSyncWords = 8 + kMaxSweepsCap;          // per op: [0] arrivals [1] abort [8+s] rotations in sweep s
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Barrier of the G CTAs working on one op; returns false if it gave up.
-__device__ bool op_barrier(unsigned* sw, int G, unsigned& gen, unsigned long long timeout_ns) {
-    __shared__ int s_ok;
-    __threadfence();
-    __syncthreads();
-    if (G == 1) return true;
-    ++gen;
-    if (threadIdx.x == 0) {
-        atomicAdd(&sw[0], 1u);
-        const unsigned target = gen * (unsigned)G;
-        const unsigned long long t0 = globaltimer_ns();
-        int ok = 1;
-        while (ld_acquire(&sw[0]) < target) {
-            if (ld_acquire(&sw[1]) != 0u) {
-                ok = 0;
-                break;
-            }
-            if (globaltimer_ns() - t0 > timeout_ns) {
-                atomicExch(&sw[1], 1u);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 __device__ __forceinline__ int tour_player(int x, int step, int cp) {
     return x == 0 ? 0 : 1 + ((x - 1 + step) % (cp - 1));
@@ -132,7 +79,6 @@ struct Ctx {
     int* rid;         // [2b] global row index or -1
     int rowlen, L;    // row length in smem (W part + Z part), W part length
     T floor2, tol;
-    T tau;            // tail threshold of this sweep: pairs of rows both below it are skipped
 };
 
 // Rotation parameters (cs, sn, t) zeroing <w_p, w_q> = g for |w_p|^2 = a,
@@ -170,62 +116,6 @@ __device__ __forceinline__ void rot_params(float a, float b, float g, float& cs,
     sn = cs * t;
 }
 
-// Tail threshold of a sweep.  With the squared row norms sorted ascending,
-// the tail is the longest run of smallest rows whose total weight is at most
-// min(cutoff/2 * total, 1/4 * a_ref), a_ref = the k_max-th largest squared
-// norm (k_max = min(chi_max, c)), leaving at least k_max rows outside it.
-// Pairs of tail rows are not rotated: the truncation discards them whatever
-// their mutual angles (their summed weight is below the cutoff), the kept
-// rows are still made orthogonal to them, and their largest singular value
-// (<= their Frobenius norm < sqrt(a_ref)/2) cannot reach the kept spectrum.
-// Returns -1 (no tail) when cutoff is 0.  All threads of the CTA call it;
-// buf is >= 2 * next_pow2(c) doubles of shared memory.
-__device__ double tail_threshold(const OpDesc& d, int c, double* buf) {
-    __shared__ double s_tau;
-    int n2 = 1;
-    while (n2 < c) n2 <<= 1;
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) buf[i] = i < c ? __ldcg(d.snorm + i) : INFINITY;
-    __syncthreads();
-    // bitonic sort, ascending
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const double x = buf[i], y = buf[l];
-                    if ((x > y) == up) {
-                        buf[i] = y;
-                        buf[l] = x;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    if (threadIdx.x == 0) {
-        double tau = -1.0;
-        const int kmax = d.chi_max < c ? d.chi_max : c;
-        if (d.cutoff > 0.0 && kmax < c) {
-            double total = 0.0;
-            for (int i = 0; i < c; ++i) total += buf[i];
-            const double aref = buf[c - kmax];
-            const double budget = fmin(0.5 * d.cutoff * total, 0.25 * aref);
-            double acc = 0.0;
-            for (int i = 0; i < c - kmax; ++i) {
-                acc += buf[i];
-                if (acc > budget) break;
-                tau = buf[i];
-            }
-        }
-        s_tau = tau;
-    }
-    __syncthreads();
-    const double t = s_tau;
-    __syncthreads();
-    return t;
-}
-
 // One warp: rows p, q (shared-memory slots).  Returns 1 if it rotated.
 template <typename T>
 __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
@@ -247,17 +137,8 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         __syncwarp();
         return 0;
     }
-    const bool ta = a <= C.tau, tb = b <= C.tau;
-    if (ta && tb) return 0;      // both in the discarded tail
     const T g = row_dot(rp, rq, C.L, lane);
-    if (g == T(0)) return 0;
-    if (ta || tb) {
-        // kept-side row vs tail row: normwise criterion (the rotation would move
-        // the larger row by less than tol of its norm)
-        if (fabs(g) <= C.tol * fmax(a, b)) return 0;
-    } else if (g * g <= C.tol * C.tol * a * b) {
-        return 0;                // relative criterion: rows that may be kept are normalised later
-    }
+    if (g == T(0) || g * g <= C.tol * C.tol * a * b) return 0;
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
@@ -355,7 +236,6 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
         const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
         C.tol = (T)tol;
-        C.tau = T(-1);
     }
 
     // squared row norms of the FP64 input (for the zero floor and the FP32 scale)
@@ -419,7 +299,6 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                 if (lane == 0) __stcg(d.snorm + row, (double)a);
             }
             if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
-            C.tau = (T)tail_threshold(d, c, reinterpret_cast<double*>(smem_raw));
             for (int r = 0; r < nbp - 1; ++r) {
                 for (int i = g; i < npair; i += G) {
                     const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);

@@ -103,7 +103,7 @@ def exported_symbols() -> list[str]:
 
 
 PROFILE_KINDS = ["merge_gate", "jacobi_svd", "truncate", "reconstruct", "trace", "measure", "build_gates",
-                 "jacobi_fp32", "precond_gemm"]
+                 "jacobi_fp32", "precond_gemm", "qr"]
 
 
 def schedule(n: int, bonds):
