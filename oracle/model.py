@@ -2,7 +2,7 @@
 
 Test infrastructure only (see ``oracle/__init__``).
 
-Conventions (readings of the paper, all listed in the design doc):
+Conventions (readings of the paper where it is silent or ambiguous):
 * sigma^+ = (sigma^x + i sigma^y)/2 (Sec. 2.1) = |0><1| in the basis where
   sigma^z|0> = +|0>; D0 (Eq. (D0)) therefore relaxes towards sigma^z = +1.
 * Eq. (K_def) is read with each *unordered* bond counted once, as in

@@ -1,7 +1,7 @@
 """Op list of one second-order Trotter step.  Test infrastructure only.
 
 The paper integrates with the W^II evolution MPO (Sec. 2.5) and is silent on a
-two-site-gate schedule; this is the reading written down in the design doc:
+two-site-gate schedule; this module takes the following reading:
 
 * The qubits sit on a 1D path (Sec. 2.5); a bond (i, j) with j = i+1 is a
   nearest-neighbour (NN) bond, j > i+1 is long-ranged along the path.

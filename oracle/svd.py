@@ -5,7 +5,7 @@ Test infrastructure only (see ``oracle/__init__``).
 App. B: after each step the Schmidt spectrum of every bond of |rho>> is
 computed and singular values are discarded under the more severe of two
 conditions, ``cut_off_rho`` (maximum discarded weight) and ``max_dim_rho``.
-Readings: the discarded weight is relative to the total weight
+Readings where the paper is silent: the discarded weight is relative to the total weight
 sum_i s_i^2; at least one value is kept; equal singular values keep their
 original order (stable sort).
 """
