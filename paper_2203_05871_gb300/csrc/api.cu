@@ -293,7 +293,10 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         fl_svd += 21.0 * nn * nn * nn;
     }
     ProfScope p_merge(c, K_MERGE);
-    CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
+    if (c->mixed)
+        CU(launch_tc_merge_gate(c->d_desc, nops, cap, c->st));
+    else
+        CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
     p_merge.stop();
 
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
@@ -430,7 +433,10 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     CU(launch_truncate(c->d_desc, nops, cap, c->st));
     p_tr.stop();
     ProfScope p_rec(c, K_RECON);
-    CU(launch_reconstruct(c->d_desc, nops, cap, c->st));
+    if (c->mixed)
+        CU(launch_tc_reconstruct(c->d_desc, nops, cap, c->st));
+    else
+        CU(launch_reconstruct(c->d_desc, nops, cap, c->st));
     p_rec.stop();
     // new bond dimensions back to the host (the next chunk's shapes depend on them)
     CU(cudaMemcpyAsync(c->h_dims.data(), c->d_dims, sizeof(int) * c->h_dims.size(), cudaMemcpyDeviceToHost,
@@ -589,6 +595,10 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
         fail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA,
              std::string("device allocation: ") + cudaGetErrorString(e));
         return bail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA);
+    }
+    if ((e = tc_prepare()) != cudaSuccess) {
+        fail(MPDO_ECUDA, std::string("tensor-core kernel set-up: ") + cudaGetErrorString(e));
+        return bail(MPDO_ECUDA);
     }
     if ((e = qr_max_resident(&c->qr_resident)) != cudaSuccess || c->qr_resident < 1) {
         fail(MPDO_ECUDA, std::string("occupancy query: ") + cudaGetErrorString(e));

@@ -107,6 +107,13 @@ size_t jacobi_sync_words_per_op();
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
 
+// tensor-core (tcgen05 kind::tf32, 3xTF32 split) merge+gate and reconstruct
+cudaError_t tc_prepare();
+cudaError_t launch_tc_merge_gate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+cudaError_t launch_tc_reconstruct(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+uint32_t tc_instr_desc_tf32(int M, int N);
+uint64_t tc_smem_desc(uint32_t saddr);
+
 int qr_threads();
 cudaError_t qr_max_resident(int* blocks);
 cudaError_t launch_qr(const OpDesc* d_desc, const int* d_cta_op, const int* d_cta_rank, const int* d_group,

@@ -242,6 +242,27 @@ def test_mixed_chi256_one_step_sampled(decay):
     assert np.abs(g - o.zz_connected(pairs)).max() <= TOL_MIXED
 
 
+def test_mixed_vs_fp64_per_observable_error():
+    """Precision comparison (N=20 chain, seeded couplings): the mixed path
+    (3xTF32 tensor-core contractions, FP32-preconditioned FP64 SVD) against the
+    FP64 path at equal chi_max and cutoff, every <Z_i> and connected <Z_i Z_j>."""
+    from paper_2203_05871_gb300 import FP64
+    wl = W.chain20_precision(chi_max=48)
+    wl = wl.with_(dt=0.02, cutoff=np.array([1e-10]))
+    steps = 25
+    pairs = all_pairs(wl.n)
+    res = {}
+    for prec in (FP64, _mixed()):
+        s = solver_for(wl, precision=prec)
+        s.step(steps)
+        res[prec] = (s.measure_1q(range(wl.n), "Z")[0], s.measure_2q(pairs, "ZZ", connected=True)[0],
+                     s.rank_log(steps)[0])
+    (z64, zz64, k64), (zm, zzm, km) = res[FP64], res[_mixed()]
+    dz, dzz = np.abs(z64 - zm).max(), np.abs(zz64 - zzm).max()
+    print(f"mixed vs fp64: max|dZ| = {dz:.2e}, max|dZZc| = {dzz:.2e}, ranks equal: {np.array_equal(k64, km)}")
+    assert dz <= TOL_MIXED and dzz <= TOL_MIXED
+
+
 def test_errors_are_codes_not_crashes():
     from paper_2203_05871_gb300 import MpdoError, Solver
     s = Solver(5, batch=1, chi_cap=8)
