@@ -235,11 +235,13 @@ def test_mixed_chi256_one_step_sampled(decay):
     st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
     o = tebd.TEBD(wl, 0, state=st)
     o.run(1, forced_k=log)
-    gz = s.measure_1q(range(n), "Z")[0]
-    assert np.abs(gz - o.z()).max() <= TOL_MIXED
+    # a random MPO is not a physical density matrix: its "expectation values"
+    # are ratios of small traces and can exceed 1, so the bound is relative
+    gz, rz = s.measure_1q(range(n), "Z")[0], o.z()
+    assert np.all(np.abs(gz - rz) <= TOL_MIXED * np.maximum(1.0, np.abs(rz)))
     pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
-    g = s.measure_2q(pairs, "ZZ", connected=True)[0]
-    assert np.abs(g - o.zz_connected(pairs)).max() <= TOL_MIXED
+    g, rg = s.measure_2q(pairs, "ZZ", connected=True)[0], o.zz_connected(pairs)
+    assert np.all(np.abs(g - rg) <= TOL_MIXED * np.maximum(1.0, np.abs(rg)))
 
 
 def test_mixed_vs_fp64_per_observable_error():
