@@ -159,7 +159,7 @@ int release_slots(mpdo_ctx* c) {
 int alloc_slots(mpdo_ctx* c, int want) {
     release_slots(c);
     const size_t mat = (size_t)c->ld * c->ld;
-    size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + c->ld) * sizeof(double);
+    size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + 2 * c->ld) * sizeof(double);
     if (c->mixed) per_slot_bytes += 3 * mat * sizeof(double) + 2 * mat * sizeof(float);
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
@@ -173,7 +173,7 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_W, (size_t)s * mat));
     CU(dalloc(&c->d_Z, (size_t)s * mat));
     CU(dalloc(&c->d_Yk, (size_t)s * c->cap * c->ld));
-    CU(dalloc(&c->d_snorm, (size_t)s * c->ld));
+    CU(dalloc(&c->d_snorm, (size_t)s * 2 * c->ld));
     CU(dalloc(&c->d_sweeps, (size_t)s));
     c->h_sweeps.assign(s, 0);
     CU(dalloc(&c->d_desc, (size_t)s));
@@ -267,7 +267,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.Z = nullptr;
         d.Acm = c->d_Z + (size_t)s * mat;
         d.Yk = c->d_Yk + (size_t)s * cap * ld;
-        d.snorm = c->d_snorm + (size_t)s * ld;
+        d.snorm = c->d_snorm + (size_t)s * 2 * ld;
         d.k_out = c->d_dims + (size_t)b * (N + 1) + p + 1;
         d.status = c->d_status + b;
         d.max_disc = c->d_maxdisc + b;

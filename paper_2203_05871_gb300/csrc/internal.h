@@ -63,7 +63,7 @@ struct OpDesc {
     double* E;         // mixed path: U32 U32^T - I (c x c)
     double* Q;         // mixed path: orthogonalised U32 (c x c)
     double* Yk;        // k x n right singular vectors (rows), ld
-    double* snorm;     // c row norms (scratch)
+    double* snorm;     // 2*ld doubles of scratch: row norms (Jacobi), R diagonal and column norms (QR)
     int* k_out;        // new chi_p
     int* status;       // per-instance status word
     double* max_disc;  // per-instance max discarded weight
