@@ -275,6 +275,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.jb = jacobi_block_rows(d.L, d.c, 8);
         d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
         d.sweeps_out = c->d_sweeps + s;
+        d.forced_k = 0;
         d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
         d.W32 = c->mixed ? c->d_W32 + (size_t)s * mat : nullptr;
         d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
@@ -411,9 +412,9 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
             const OpDesc& d = c->h_desc[s];
             maxc = std::max(maxc, d.c);
             maxL = std::max(maxL, d.L);
-            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1};
-            g2[s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0};
-            g3[s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0};
+            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0};
+            g2[s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0, 0};
+            g3[s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0, 0};
             fl_gemm += 2.0 * d.c * d.c * d.c * 2 + 2.0 * d.c * d.c * d.L;
         }
         CU(cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(GemmDesc) * 3 * c->slots, cudaMemcpyHostToDevice, c->st));

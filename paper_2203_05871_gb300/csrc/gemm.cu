@@ -1,7 +1,8 @@
 // Batched small dense GEMMs of the mixed-precision SVD preconditioner.
 //
-//   C = alpha * op(A) B' + beta * D  (- I if sub_identity)
-// with A (M x K) and B (K x N, or N x K when b_trans) row-major, stored as
+//   C = alpha * op(A) op(B) + beta * D  (- I if sub_identity)
+// with A (M x K, or K x M when a_trans) and B (K x N, or N x K when b_trans)
+// row-major, stored as
 // float or double (converted on load), accumulated in TC (double or float),
 // written as double.  One launch serves a list of problems of different
 // sizes (grid.z = problem); CTAs outside a problem's tiles return at once.
@@ -34,10 +35,18 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* descs) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) acc[u][v] = (TC)0;
     for (int k0 = 0; k0 < g.K; k0 += GK) {
-        for (int e = t; e < GT * GK; e += 256) {
-            const int ii = e / GK, kk = e % GK;
-            const int gi = i0 + ii, gk = k0 + kk;
-            As[kk][ii] = (gi < g.M && gk < g.K) ? load_as<TC>(g.A, g.a_f32, (size_t)gi * g.lda + gk) : (TC)0;
+        if (g.a_trans) {   // A stored K x M row-major
+            for (int e = t; e < GT * GK; e += 256) {
+                const int kk = e / GT, ii = e % GT;
+                const int gi = i0 + ii, gk = k0 + kk;
+                As[kk][ii] = (gi < g.M && gk < g.K) ? load_as<TC>(g.A, g.a_f32, (size_t)gk * g.lda + gi) : (TC)0;
+            }
+        } else {
+            for (int e = t; e < GT * GK; e += 256) {
+                const int ii = e / GK, kk = e % GK;
+                const int gi = i0 + ii, gk = k0 + kk;
+                As[kk][ii] = (gi < g.M && gk < g.K) ? load_as<TC>(g.A, g.a_f32, (size_t)gi * g.lda + gk) : (TC)0;
+            }
         }
         if (g.b_trans) {
             for (int e = t; e < GT * GK; e += 256) {

@@ -69,6 +69,7 @@ struct OpDesc {
     double* max_disc;  // per-instance max discarded weight
     int* rank_log;     // &log[b][step*n_ops + op] or nullptr
     int* sweeps_out;   // Jacobi sweeps used (or nullptr)
+    int forced_k;      // > 0: truncation rank imposed (replay of a recorded run)
 };
 
 // ---------------------------------------------------------------------------
@@ -132,6 +133,7 @@ struct GemmDesc {
     const void* D;
     int ldd, d_f32;
     int sub_identity;
+    int a_trans;      // A stored K x M (default 0)
 };
 cudaError_t launch_gemm(const GemmDesc* d_desc, int count, int max_m, int max_n, bool fp32_compute,
                         cudaStream_t st);

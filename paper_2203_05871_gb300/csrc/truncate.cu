@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(TT) truncate_kernel(const OpDesc* descs, int c
             }
             k = kcut;
             if (k > d.chi_max) k = d.chi_max;
+            if (d.forced_k > 0) k = d.forced_k;
             if (k > c) k = c;
             if (k < 1) k = 1;
             double dsum = 0.0;
