@@ -150,6 +150,15 @@ int mpdo_op_counts(mpdo_ctx *ctx, int *n_ops, int *n_swaps, int *n_layers);
  * call, [B][n_steps * n_ops] in step order.  cap = capacity of k in ints. */
 int mpdo_rank_log(mpdo_ctx *ctx, int *k, long long cap);
 
+/* Impose the truncation ranks of the next mpdo_trotter_step calls (frozen-rank
+ * mode, App. B's rule replaced by a recorded sequence): k is host memory,
+ * [B][n_steps][n_ops] in the layout of mpdo_rank_log; step s of every later
+ * mpdo_trotter_step call (counted from that call's first step) uses row s, steps
+ * beyond n_steps use the rule.  Each k must be in [1, chi_max of its instance];
+ * an op never keeps more values than its bond matrix has.  k = NULL or
+ * n_steps <= 0 clears.  mpdo_build_gates clears as well.  Used for finite-
+ * difference gradients, which need the ranks held fixed.  EINVAL, ESTATE. */
+int mpdo_force_ranks(mpdo_ctx *ctx, const int *k, int n_steps);
 /* Copy instance b's gate matrices out: [n_ops][16][16] row-major doubles in
  * step order (swaps included), host memory, cap = capacity in doubles. */
 int mpdo_gates(mpdo_ctx *ctx, int b, double *out, long long cap);
@@ -201,6 +210,44 @@ int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds, long 
 int mpdo_measure_1q_noalloc(const double *sites, const int *dims, int n_qubits, int batch, int chi_cap,
                             const int *qubits, int nq, char comp, double *out, void *cuda_stream);
 
+/* Reverse-mode gradient of the observables with respect to the model
+ * parameters (the paper has no gradient; this differentiates the update of
+ * App. B as implemented here, with the ranks of the forward run held fixed).
+ *
+ * mpdo_grad_forward advances every instance by n_steps Trotter steps exactly
+ * as mpdo_trotter_step does, and keeps what the backward pass needs: a device
+ * checkpoint of the state at the start of every step (compact site tensors,
+ * Schmidt weights, bond dimensions: about sum_p 4 chi_p chi_{p+1} doubles per
+ * instance and step), the trace divided out after each step and the rank of
+ * every truncation.  The checkpoints are allocated by this call and kept until
+ * the next mpdo_grad_forward or mpdo_destroy.  The observables at the final
+ * time are then read with mpdo_measure_1q / mpdo_measure_2q as usual.
+ *
+ * mpdo_grad_backward returns, per instance b, the gradient of
+ *   L_b = sum_i zbar[b][i] <sigma^z_i>
+ *       + sum_{i<j} wbar[b][i][j] (<sigma^z_i sigma^z_j> - <sigma^z_i><sigma^z_j>)
+ * at the final time of the last mpdo_grad_forward (Eq. (mu), Eq. (etadef)):
+ * zbar is [B][N] and wbar [B][N][N] host arrays (only the entries i < j of wbar
+ * are read; either may be NULL = 0), i.e. the cotangents of the observables,
+ * as in a vector-Jacobian product.  grad is [B][6N + 2 n_bonds] host memory,
+ * packed like the model: d/dh_x[N], d/dh_y[N], d/dh_z[N], d/dg0[N], d/dg1[N],
+ * d/dg2[N], d/dJ[n_bonds], d/dJz[n_bonds].  loss (host [B], may be NULL)
+ * receives L_b.  The pass recomputes every step from its checkpoint with the
+ * recorded ranks, differentiates each op (gate contraction, weighting, the
+ * truncated SVD with Lorentzian-broadened 1/(s_j^2 - s_i^2), width 1e-12 s_0^2)
+ * and maps the gate cotangents to the parameters through the Frechet
+ * derivative of exp.  Afterwards the context again holds the final state.
+ * Accuracy: FP64; the truncated-SVD backward divides by gaps s_j^2 - s_i^2 and
+ * by kept s_j^2, so kept singular values far below the largest (a cutoff much
+ * under 1e-10) amplify the rounding of the forward SVD.
+ * Errors: ESTATE without a preceding mpdo_grad_forward or after the state
+ * changed (step, set_state, build_gates); EINVAL for non-finite weights;
+ * ENOMEM; the status errors of mpdo_trotter_step.
+ *
+ * mpdo_grad = mpdo_grad_forward then mpdo_grad_backward. */
+int mpdo_grad_forward(mpdo_ctx *ctx, int n_steps);
+int mpdo_grad_backward(mpdo_ctx *ctx, const double *zbar, const double *wbar, double *grad, double *loss);
+int mpdo_grad(mpdo_ctx *ctx, int n_steps, const double *zbar, const double *wbar, double *grad, double *loss);
 /* Message of the last error on this thread ("" if none). */
 const char *mpdo_last_error(void);
 

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx.h"
 #include "internal.h"
 
 using namespace mpdo;
@@ -23,30 +24,14 @@ namespace mpdo {
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace mpdo
 
-namespace {
-constexpr int kProfKinds = 10;
-enum { K_MERGE = 0, K_JACOBI = 1, K_TRUNC = 2, K_RECON = 3, K_TRACE = 4, K_MEASURE = 5, K_GATES = 6, K_JACOBI32 = 7,
-       K_GEMM = 8, K_QR = 9 };
-
+namespace mpdo {
 int fail(int code, const std::string& msg) {
     g_err = msg;
     return code;
 }
+}  // namespace mpdo
 
-#define CU(call)                                                                               \
-    do {                                                                                       \
-        cudaError_t e_ = (call);                                                               \
-        if (e_ != cudaSuccess)                                                                 \
-            return fail(MPDO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));       \
-    } while (0)
-
-template <class T>
-cudaError_t dalloc(T** p, size_t count) {
-    *p = nullptr;
-    if (count == 0) count = 1;
-    return cudaMalloc((void**)p, count * sizeof(T));
-}
-
+namespace {
 // rho(t0) site vectors: v[b][q][4] -> site (b, q), element [0][s][0]
 __global__ void init_product_kernel(double* sites, const double* v, int N, int cap) {
     const int b = blockIdx.x, q = threadIdx.x;
@@ -57,93 +42,36 @@ __global__ void init_product_kernel(double* sites, const double* v, int N, int c
 
 }  // namespace
 
-struct mpdo_ctx {
-    mpdo_config cfg{};
-    cudaStream_t st = nullptr;
-    int dev = 0;
-    int N = 0, B = 0, cap = 0, ld = 0;
-    bool built = false;
-    // schedule
-    std::vector<Layer> layers;
-    std::vector<double> weights;
-    std::vector<int> layer_op0;   // op index of each layer's first op
-    int n_ops = 0, n_swaps = 0, max_layer = 0;
-    int nb = 0;
-    std::vector<int> chi_max;
-    std::vector<double> cutoff;
-    // state (device)
-    double* d_sites = nullptr;    // [B][N][cap][4][cap]
-    double* d_lam = nullptr;      // [B][N][cap]   lambda_p for p = 0..N-2
-    int* d_dims = nullptr;        // [B][N+1]
-    int* d_status = nullptr;      // [B]
-    double* d_maxdisc = nullptr;  // [B]
-    double* d_trace = nullptr;    // [B]
-    double* d_params = nullptr;   // [B][6N + 2nb]
-    double* d_gates = nullptr;    // [B][n_ops][256]
-    GateSpec* d_specs = nullptr;
-    // per-slot workspaces
-    int slots = 0;
-    double *d_thetap = nullptr, *d_W = nullptr, *d_Z = nullptr, *d_Yk = nullptr, *d_snorm = nullptr;
-    int* d_sweeps = nullptr;      // [slots] Jacobi sweeps of the last chunk
-    bool mixed = false;           // mixed-precision SVD (FP32 preconditioning + FP64 finish)
-    double *d_W0 = nullptr, *d_E = nullptr, *d_Q = nullptr;
-    float *d_W32 = nullptr, *d_U32 = nullptr;
-    GemmDesc* d_gemm = nullptr;
-    GemmDesc* h_gemm = nullptr;   // pinned, [3][slots]
-    std::vector<int> h_sweeps;
-    long long prof_sweeps = 0, prof_svds = 0, prof_sweeps32 = 0;
-    OpDesc* d_desc = nullptr;
-    OpDesc* h_desc = nullptr;     // pinned
-    int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]
-    unsigned* d_sync = nullptr;
-    int jacobi_resident = 0;
-    int qr_resident = 0;
-    // measurement
-    double *d_envL = nullptr, *d_envR = nullptr, *d_full = nullptr, *d_one_a = nullptr, *d_one_b = nullptr,
-           *d_out = nullptr;
-    int *d_q = nullptr, *d_pairs = nullptr;
-    unsigned char* d_need = nullptr;
-    // host mirrors
-    std::vector<int> h_dims;
-    std::vector<int> rank_log;    // [B][steps*n_ops] of the last trotter_step call
-    int rank_steps = 0;
-    // profiling
-    bool prof = false;
-    cudaEvent_t ev[2 * kProfKinds] = {};
-    double prof_ms[kProfKinds] = {};
-    long long prof_launch[kProfKinds] = {};
-    double prof_flops[kProfKinds] = {};
-};
 
-namespace {
+namespace mpdo {
 
 void free_all(mpdo_ctx* c) {
-    void* ptrs[] = {c->d_sites, c->d_lam,   c->d_dims,  c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
-                    c->d_gates, c->d_specs, c->d_thetap, c->d_W,     c->d_Z,       c->d_Yk,    c->d_snorm,
-                    c->d_desc,  c->d_cta,   c->d_sync,  c->d_envL,   c->d_envR,    c->d_full,  c->d_one_a,
-                    c->d_one_b, c->d_out,   c->d_q,     c->d_pairs,  c->d_need};
+    release_slots(c);
+    void* ptrs[] = {c->d_sites, c->d_lam,  c->d_dims, c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
+                    c->d_gates, c->d_specs, c->d_envL, c->d_envR,  c->d_full,    c->d_one_a, c->d_one_b,
+                    c->d_out,   c->d_q,     c->d_pairs, c->d_need};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    if (c->h_desc) cudaFreeHost(c->h_desc);
-    if (c->h_cta) cudaFreeHost(c->h_cta);
     for (auto& e : c->ev)
         if (e) cudaEventDestroy(e);
+    if (c->grad) grad_free(c->grad);
+    c->grad = nullptr;
 }
-
-size_t site_elems(const mpdo_ctx* c) { return (size_t)c->cap * 4 * c->cap; }
-double* site(mpdo_ctx* c, int b, int p) { return c->d_sites + ((size_t)b * c->N + p) * site_elems(c); }
 
 int release_slots(mpdo_ctx* c) {
     void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps,
-                    c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm};
+                    c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm, c->d_copy};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
     c->d_W0 = c->d_E = c->d_Q = nullptr;
     c->d_W32 = c->d_U32 = nullptr;
     c->d_gemm = nullptr;
+    c->d_copy = nullptr;
     if (c->h_gemm) cudaFreeHost(c->h_gemm);
     c->h_gemm = nullptr;
+    if (c->h_copy) cudaFreeHost(c->h_copy);
+    c->h_copy = nullptr;
     c->d_desc = nullptr;
     c->d_cta = nullptr;
     c->d_sync = nullptr;
@@ -155,6 +83,10 @@ int release_slots(mpdo_ctx* c) {
     c->slots = 0;
     return MPDO_OK;
 }
+
+}  // namespace mpdo
+
+namespace {
 
 int alloc_slots(mpdo_ctx* c, int want) {
     release_slots(c);
@@ -182,6 +114,8 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_sync, (size_t)s * jacobi_sync_words_per_op()));
     CU(cudaMallocHost((void**)&c->h_desc, sizeof(OpDesc) * s));
     CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * 3 * (2 * gcap + s)));
+    CU(dalloc(&c->d_copy, (size_t)4 * s));
+    CU(cudaMallocHost((void**)&c->h_copy, sizeof(Copy2D) * 4 * s));
     if (c->mixed) {
         CU(dalloc(&c->d_W0, (size_t)s * mat));
         CU(dalloc(&c->d_E, (size_t)s * mat));
@@ -194,18 +128,9 @@ int alloc_slots(mpdo_ctx* c, int want) {
     return MPDO_OK;
 }
 
-// Bracket a launch with events when profiling; prof_end reads the time after
-// a stream synchronisation (so only call it where the host waits anyway).
-struct ProfScope {
-    mpdo_ctx* c;
-    int k;
-    ProfScope(mpdo_ctx* c_, int k_) : c(c_), k(k_) {
-        if (c->prof) cudaEventRecord(c->ev[2 * k], c->st);
-    }
-    void stop() {
-        if (c->prof) cudaEventRecord(c->ev[2 * k + 1], c->st);
-    }
-};
+}  // namespace
+
+namespace mpdo {
 
 void prof_collect(mpdo_ctx* c, int k, double flops) {
     if (!c->prof) return;
@@ -229,12 +154,8 @@ int check_status_code(mpdo_ctx* c) {
     return MPDO_OK;
 }
 
-// One chunk of (instance, op) work items of a layer.
-struct Item {
-    int b, layer, idx;
-};
-
-int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
+int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,
+              bool log_ranks) {
     const int nops = (int)items.size();
     const int N = c->N, cap = c->cap, ld = c->ld;
     const size_t mat = (size_t)ld * ld;
@@ -275,7 +196,12 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         d.jb = jacobi_block_rows(d.L, d.c, 8);
         d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
         d.sweeps_out = c->d_sweeps + s;
-        d.forced_k = 0;
+        int fk = forced ? forced[s] : 0;
+        if (!forced && step < c->forced_steps)
+            fk = c->forced[((size_t)b * c->forced_steps + step) * c->n_ops + d.op];
+        d.forced_k = fk;
+        d.tape_V = tape ? tape[s].V : nullptr;
+        d.tape_s = tape ? tape[s].s : nullptr;
         d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
         d.W32 = c->mixed ? c->d_W32 + (size_t)s * mat : nullptr;
         d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
@@ -286,6 +212,25 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
         qwork[s] = (double)d.m * d.n * d.c;
     }
     CU(cudaMemcpyAsync(c->d_desc, c->h_desc, sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
+    if (tape) {
+        // inputs of every op (sites p, p+1, lambda_{p-1}) before the merge
+        // overwrites them, and Theta' after it
+        Copy2D* hc = c->h_copy;
+        int nc = 0, max_rows = 1;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            hc[nc++] = Copy2D{d.A, tape[s].A, 4 * d.cl, d.cm, cap, d.cm, 1.0};
+            hc[nc++] = Copy2D{d.B, tape[s].B, 4 * d.cm, d.cr, cap, d.cr, 1.0};
+            if (d.lam_left) hc[nc++] = Copy2D{d.lam_left, tape[s].lam, 1, d.cl, cap, d.cl, 1.0};
+            max_rows = std::max(max_rows, 4 * std::max(d.cl, d.cm));
+        }
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            hc[nc + s] = Copy2D{d.thetap, tape[s].thetap, d.m, d.n, ld, d.n, 1.0};
+        }
+        CU(cudaMemcpyAsync(c->d_copy, hc, sizeof(Copy2D) * (nc + nops), cudaMemcpyHostToDevice, c->st));
+        CU(launch_copy2d(c->d_copy, nc, max_rows, c->st));
+    }
     double fl_merge = 0.0, fl_svd = 0.0;
     for (int s = 0; s < nops; ++s) {
         const OpDesc& d = c->h_desc[s];
@@ -299,6 +244,15 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     else
         CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
     p_merge.stop();
+    if (tape) {
+        int nc = 0, max_rows = 1;
+        for (int s = 0; s < nops; ++s) {
+            const OpDesc& d = c->h_desc[s];
+            nc += 2 + (d.lam_left ? 1 : 0);
+            max_rows = std::max(max_rows, d.m);
+        }
+        CU(launch_copy2d(c->d_copy + nc, nops, max_rows, c->st));
+    }
 
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
     const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), c->slots);
@@ -464,7 +418,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     }
     prof_collect(c, K_TRUNC, 0.0);
     prof_collect(c, K_RECON, fl_rec);
-    for (int s = 0; s < nops; ++s) {
+    for (int s = 0; s < nops && log_ranks; ++s) {
         const Item& it = items[s];
         const Op& op = c->layers[it.layer][it.idx];
         const int k = c->h_dims[(size_t)it.b * (N + 1) + op.p + 1];
@@ -473,6 +427,19 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step) {
     }
     return MPDO_OK;
 }
+
+int normalize_trace(mpdo_ctx* c) {
+    ProfScope p_trace(c, K_TRACE);
+    CU(launch_trace_normalize(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
+                              c->d_status, c->st));
+    p_trace.stop();
+    prof_collect(c, K_TRACE, 0.0);
+    return MPDO_OK;
+}
+
+}  // namespace mpdo
+
+namespace {
 
 int validate_model(mpdo_ctx* c, const mpdo_model* m) {
     const int N = c->N, B = c->B;
@@ -714,6 +681,9 @@ int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
     CU(cudaMemsetAsync(c->d_trace, 0, sizeof(double) * B, c->st));
     CU(cudaStreamSynchronize(c->st));
     c->built = true;
+    ++c->gen;
+    c->forced.clear();
+    c->forced_steps = 0;
     return MPDO_OK;
 }
 
@@ -724,6 +694,7 @@ int mpdo_trotter_step(mpdo_ctx* c, int n_steps) {
     if (n_steps < 0) return fail(MPDO_EINVAL, "n_steps must be >= 0");
     c->rank_steps = n_steps;
     c->rank_log.assign((size_t)c->B * n_steps * c->n_ops, 0);
+    ++c->gen;
     for (int step = 0; step < n_steps; ++step) {
         for (int li = 0; li < (int)c->layers.size(); ++li) {
             std::vector<Item> items;
@@ -732,15 +703,12 @@ int mpdo_trotter_step(mpdo_ctx* c, int n_steps) {
             for (size_t s0 = 0; s0 < items.size(); s0 += c->slots) {
                 std::vector<Item> chunk(items.begin() + s0,
                                         items.begin() + std::min(items.size(), s0 + (size_t)c->slots));
-                int rc = run_chunk(c, chunk, step);
+                int rc = run_chunk(c, chunk, step, nullptr, nullptr, true);
                 if (rc) return rc;
             }
         }
-        ProfScope p_trace(c, K_TRACE);
-        CU(launch_trace_normalize(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
-                                  c->d_status, c->st));
-        p_trace.stop();
-        prof_collect(c, K_TRACE, 0.0);
+        int rc = normalize_trace(c);
+        if (rc) return rc;
     }
     return check_status_code(c);
 }
@@ -860,6 +828,7 @@ int mpdo_set_state(mpdo_ctx* c, int b, const int* dims, const double* tensors) {
     for (int p = 0; p <= N; ++p) c->h_dims[(size_t)b * (N + 1) + p] = dims[p];
     CU(cudaMemcpyAsync(c->d_dims, c->h_dims.data(), sizeof(int) * c->h_dims.size(), cudaMemcpyHostToDevice, c->st));
     CU(cudaStreamSynchronize(c->st));
+    ++c->gen;
     return MPDO_OK;
 }
 
@@ -902,6 +871,25 @@ int mpdo_rank_log(mpdo_ctx* c, int* k, long long cap) {
     if (!c || !k) return fail(MPDO_EINVAL, "NULL argument");
     if ((long long)c->rank_log.size() > cap) return fail(MPDO_ECAPACITY, "rank log buffer too small");
     std::copy(c->rank_log.begin(), c->rank_log.end(), k);
+    return MPDO_OK;
+}
+
+int mpdo_force_ranks(mpdo_ctx* c, const int* k, int n_steps) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    if (!k || n_steps <= 0) {
+        c->forced.clear();
+        c->forced_steps = 0;
+        return MPDO_OK;
+    }
+    const size_t per_b = (size_t)n_steps * c->n_ops;
+    for (int b = 0; b < c->B; ++b)
+        for (size_t i = 0; i < per_b; ++i) {
+            const int v = k[(size_t)b * per_b + i];
+            if (v < 1 || v > c->chi_max[b]) return fail(MPDO_EINVAL, "forced rank outside [1, chi_max]");
+        }
+    c->forced.assign(k, k + (size_t)c->B * per_b);
+    c->forced_steps = n_steps;
     return MPDO_OK;
 }
 

@@ -70,6 +70,8 @@ struct OpDesc {
     int* rank_log;     // &log[b][step*n_ops + op] or nullptr
     int* sweeps_out;   // Jacobi sweeps used (or nullptr)
     int forced_k;      // > 0: truncation rank imposed (replay of a recorded run)
+    double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr
+    double* tape_s;    // adjoint recompute: all c sorted singular values
 };
 
 // ---------------------------------------------------------------------------
@@ -155,5 +157,64 @@ cudaError_t launch_measure_2q(const double* sites, const int* dims, int n, int B
 cudaError_t launch_gather_2q(const double* full, const double* one_a, const double* one_b,
                              const int* d_trip, int m, int np, int n, int B, int connected,
                              double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// adjoint (reverse mode through the Trotter sweep; adjoint.cu)
+// ---------------------------------------------------------------------------
+// Batched strided copy: dst[i][j] = scale * src[i][j] (src == nullptr: 0),
+// i < rows, j < cols.  One launch serves count copies (grid.y = copy).
+struct Copy2D {
+    const double* src;
+    double* dst;
+    int rows, cols, src_ld, dst_ld;
+    double scale;
+};
+cudaError_t launch_copy2d(const Copy2D* d_desc, int count, int max_rows, cudaStream_t st);
+
+// One op of the backward sweep.  Matrices are compact row-major (leading
+// dimension = row length); m = 4 cl, n = 4 cr, c = min(m, n), k = new chi_p.
+struct BwdDesc {
+    int cl, cm, cr, m, n, c, k;
+    int is_gate;            // 0 for swaps (no parameter gradient)
+    const double* G;        // the op's 16 x 16 gate
+    const double* thetap;   // Theta' (m x n)
+    const double* V;        // c x n sorted right singular vectors (rows)
+    const double* s;        // c sorted singular values
+    const double* lam;      // lambda_{p-1} (cl) or nullptr (p == 0)
+    const double* sbar;     // cotangent of lambda_p (k)
+    double* lbar_left;      // cotangent of lambda_{p-1} (cl), accumulated; nullptr when p == 0
+    double* Vbar;           // k x n: cotangent of V_k^T, then scaled by 1/s_j^2
+    double* K;              // c x k: V V-bar^T
+    double* Om;             // c x k: Lorentzian-broadened F o K, zero diagonal
+    double* Mk;             // k x c: Om^T - S_k^-2 K^T + diag(s-bar / s)
+    double* S2;             // 2k x n: [V_k ; Om^T V]
+    double* S3;             // 2k x n: [H_k ; V_k]
+    double* X1;             // m x n: Theta' H, then Theta = A B
+    double* X2;             // m x n: Theta'-bar, then Theta-bar
+    double* gpart;          // [parts][256] partial G-bar sums of this launch
+    double* gacc;           // [256] G-bar of the op, accumulated over steps
+};
+cudaError_t launch_svd_bwd_coeffs(const BwdDesc* d_desc, int nops, double rel_broadening, cudaStream_t st);
+cudaError_t launch_lambda_bwd(const BwdDesc* d_desc, int nops, int max_cl, cudaStream_t st);
+cudaError_t launch_gate_bwd(const BwdDesc* d_desc, int nops, int parts, cudaStream_t st);
+constexpr int kGateBwdParts = 32;
+
+// Loss cotangent at the final state: for L = sum_i a_i <z_i> + sum_{i<j}
+// W_ij (<z_i z_j> - <z_i><z_j>), writes dL/dB_k into sbar (site layout) for
+// every instance and site, and coef[b] = (b_0..b_{N-1}, c, E(I), L).
+// a [B][N], W [B][N][N] symmetric with zero diagonal.
+struct LossScratch {
+    double *L0, *L1, *L2, *R0, *R1, *R2, *T, *coef;
+};
+cudaError_t launch_loss_cotangent(const double* sites, const int* dims, int n, int B, int chi_cap, const double* a,
+                                  const double* W, const LossScratch& s, double* sbar, cudaStream_t st);
+
+// Parameter gradient from the accumulated G-bar of every (instance, op):
+// X-bar = Frechet derivative of exp at (tau L_op)^T applied to G-bar (top
+// right block of exp([[X^T, G-bar], [0, X^T]])), L-bar = tau X-bar, then
+// dL/dtheta = <L-bar, dL_op/dtheta>.  grad [B][6n + 2nb] in the packing of
+// the parameters (h_x, h_y, h_z, g0, g1, g2 per qubit, J, Jz per bond).
+cudaError_t launch_param_grad(const GateSpec* d_specs, int count, int n, int nb, const double* d_params,
+                              const double* gacc, double* contrib, int B, int n_ops, double* grad, cudaStream_t st);
 
 }  // namespace mpdo

@@ -5,7 +5,10 @@
 // sum_{i>=k} s_i^2 is <= cutoff * sum_i s_i^2 (the tail is summed from the
 // smallest value up); k = min(chi_max, k_cut).  Writes lambda_p = s[:k],
 // Yk[j] = v_j^T (rows of W normalised, or rows of Z), the new site p+1
-// B'[j][s2][r] = Yk[j][s2*cr + r] and the new bond dimension.
+// B'[j][s2][r] = Yk[j][s2*cr + r] and the new bond dimension.  A forced rank
+// (replay of a recorded run) replaces k_cut, still capped by chi_max and c.
+// When the adjoint records a tape, all c sorted singular values and
+// normalised rows are written as well.
 #include <mpdo.h>
 
 #include "internal.h"
@@ -89,7 +92,7 @@ __global__ void __launch_bounds__(TT) truncate_kernel(const OpDesc* descs, int c
             }
             k = kcut;
             if (k > d.chi_max) k = d.chi_max;
-            if (d.forced_k > 0) k = d.forced_k;
+            if (d.forced_k > 0) k = d.forced_k < d.chi_max ? d.forced_k : d.chi_max;
             if (k > c) k = c;
             if (k < 1) k = 1;
             double dsum = 0.0;
@@ -109,6 +112,18 @@ __global__ void __launch_bounds__(TT) truncate_kernel(const OpDesc* descs, int c
     __syncthreads();
     const int k = s_k;
     for (int j = threadIdx.x; j < k; j += TT) d.lam_out[j] = bad ? 0.0 : s[perm[j]];
+    if (d.tape_V) {
+        // every sorted right singular vector (zero rows stay zero) for the adjoint
+        for (int j = threadIdx.x; j < c; j += TT) d.tape_s[j] = bad ? 0.0 : s[perm[j]];
+        for (int j = warp; j < c; j += TT / 32) {
+            const int src = perm[j];
+            const double sv = s[src];
+            const double inv = (sv > 0.0 && !bad) ? 1.0 / sv : 0.0;
+            const double* wr = d.W + (size_t)src * ld;
+            double* v = d.tape_V + (size_t)j * d.n;
+            for (int i = lane; i < d.n; i += 32) v[i] = wr[i] * inv;
+        }
+    }
     const int n = d.n, cr = d.cr;
     for (int j = warp; j < k; j += TT / 32) {
         const int src = perm[j];

@@ -83,6 +83,10 @@ def load_library(path: str = LIB_PATH):
                                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
         "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
+        "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
+        "mpdo_grad_forward": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mpdo_grad_backward": (ctypes.c_int, [vp, _dp, _dp, _dp, _dp]),
+        "mpdo_grad": (ctypes.c_int, [vp, ctypes.c_int, _dp, _dp, _dp, _dp]),
         "mpdo_last_error": (ctypes.c_char_p, []),
         "mpdo_destroy": (None, [vp]),
     }
@@ -98,8 +102,9 @@ def exported_symbols() -> list[str]:
     """Names declared in include/mpdo.h (for the export test)."""
     return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
-            "mpdo_rank_log", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable", "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc",
-            "mpdo_last_error", "mpdo_destroy"]
+            "mpdo_rank_log", "mpdo_force_ranks", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
+            "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
 PROFILE_KINDS = ["merge_gate", "jacobi_svd", "truncate", "reconstruct", "trace", "measure", "build_gates",
@@ -212,6 +217,7 @@ class Solver:
             init = "".join(s.lower() for s in wl.init).encode()
         m.init_pauli = init
         _check(self._lib.mpdo_build_gates(self._h, ctypes.byref(m), float(wl.dt if dt is None else dt)))
+        self._n_bonds = len(wl.bonds)
 
     def step(self, n_steps: int = 1, check: bool = True):
         rc = self._lib.mpdo_trotter_step(self._h, int(n_steps))
@@ -307,3 +313,36 @@ class Solver:
         buf = np.zeros(self.batch * n_steps * n_ops, np.int32)
         _check(self._lib.mpdo_rank_log(self._h, _ptr(buf, ctypes.c_int), len(buf)))
         return buf.reshape(self.batch, n_steps * n_ops)
+
+    def force_ranks(self, ranks=None):
+        """Hold the truncation ranks of the next steps fixed: ranks is
+        [B, n_steps * n_ops] (the layout of rank_log); None clears."""
+        if ranks is None:
+            _check(self._lib.mpdo_force_ranks(self._h, None, 0))
+            return
+        n_ops = self.op_counts()[0]
+        r = _as(ranks, np.int32).reshape(self.batch, -1)
+        assert r.shape[1] % n_ops == 0
+        _check(self._lib.mpdo_force_ranks(self._h, _ptr(r, ctypes.c_int), r.shape[1] // n_ops))
+
+    # -- adjoint ----------------------------------------------------------
+    def n_params(self):
+        return 6 * self.n + 2 * self._n_bonds
+
+    def grad_forward(self, n_steps: int):
+        """n_steps Trotter steps with per-step checkpoints for grad_backward."""
+        _check(self._lib.mpdo_grad_forward(self._h, int(n_steps)))
+
+    def grad_backward(self, zbar=None, wbar=None):
+        """Gradient of sum_i zbar[b,i] <z_i> + sum_{i<j} wbar[b,i,j] conn_ij at
+        the final time of the last grad_forward.  Returns (grad [B, 6N+2nb],
+        loss [B]); grad is packed (h_x, h_y, h_z, g0, g1, g2 per qubit, J, Jz per bond)."""
+        B, N = self.batch, self.n
+        zb = None if zbar is None else _as(zbar, np.float64).reshape(B, N)
+        wb = None if wbar is None else _as(wbar, np.float64).reshape(B, N, N)
+        g = np.zeros((B, self.n_params()))
+        loss = np.zeros(B)
+        _check(self._lib.mpdo_grad_backward(self._h, None if zb is None else _ptr(zb, ctypes.c_double),
+                                            None if wb is None else _ptr(wb, ctypes.c_double),
+                                            _ptr(g, ctypes.c_double), _ptr(loss, ctypes.c_double)))
+        return g, loss
