@@ -234,7 +234,8 @@ int mpdo_measure_1q_noalloc(const double *sites, const int *dims, int n_qubits, 
  * d/dg2[N], d/dJ[n_bonds], d/dJz[n_bonds].  loss (host [B], may be NULL)
  * receives L_b.  The pass recomputes every step from its checkpoint with the
  * recorded ranks, differentiates each op (gate contraction, weighting, the
- * truncated SVD with Lorentzian-broadened 1/(s_j^2 - s_i^2), width 1e-12 s_0^2)
+ * truncated SVD with Lorentzian-broadened 1/(s_j^2 - s_i^2), width 1e-12 s_0^2,
+ * pairs equal to 1e-10 relative treated as one degenerate subspace)
  * and maps the gate cotangents to the parameters through the Frechet
  * derivative of exp.  Afterwards the context again holds the final state.
  * Accuracy: FP64; the truncated-SVD backward divides by gaps s_j^2 - s_i^2 and

@@ -15,6 +15,7 @@
 //                  K = V_c^T V-bar_k,  Om_ij = F_ij K_ij (i != j),
 //                  F_ij = 1/(s_j^2 - s_i^2), Lorentzian-broadened to
 //                  D/(D^2 + delta^2), D = s_j^2 - s_i^2, delta = eps s_0^2,
+//                  and 0 inside a degenerate pair (|s_i - s_j| <= 1e-10 max),
 //                so theta~-bar = D [(Theta' V_k) H_k + (Theta' V_c Om) V_k^T]
 //                with H_k = Mk V_c^T + S_k^-2 V-bar_k^T, Mk = Om^T - S_k^-2 K^T + diag(s-bar/s);
 //                Theta'-bar = D theta~-bar + B-bar_p' V_k^T,
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(CT) copy2d_kernel(const Copy2D* descs) {
 // ---------------------------------------------------------------------------
 // truncated-SVD backward: Om, Mk, V-bar scaling, stacked operands
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(CT) svd_bwd_coeffs_kernel(const BwdDesc* descs, double eps) {
+__global__ void __launch_bounds__(CT) svd_bwd_coeffs_kernel(const BwdDesc* descs, double eps, double deg_tol) {
     const BwdDesc& d = descs[blockIdx.y];
     const int c = d.c, k = d.k, n = d.n;
     const double s0 = d.s[0];
@@ -84,8 +85,12 @@ __global__ void __launch_bounds__(CT) svd_bwd_coeffs_kernel(const BwdDesc* descs
             const double kij = d.K[e];
             const double si = d.s[i], sj = d.s[j];
             const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
+            // pairs equal to deg_tol (relative) span one degenerate subspace:
+            // the loss does not change under rotations inside it, so the
+            // exact coefficient is 0 (rounding splits such pairs by ~1 ulp,
+            // and 1/(s_j^2 - s_i^2) would amplify rounding noise instead)
             double om = 0.0;
-            if (i != j) {
+            if (i != j && !(fabs(sj - si) <= deg_tol * fmax(si, sj))) {
                 const double D = sj * sj - si * si;
                 const double den = D * D + delta * delta;
                 om = den > 0.0 ? D / den * kij : 0.0;
@@ -570,9 +575,10 @@ cudaError_t launch_copy2d(const Copy2D* d_desc, int count, int max_rows, cudaStr
     return cudaSuccess;
 }
 
-cudaError_t launch_svd_bwd_coeffs(const BwdDesc* d_desc, int nops, double rel_broadening, cudaStream_t st) {
+cudaError_t launch_svd_bwd_coeffs(const BwdDesc* d_desc, int nops, double rel_broadening, double rel_degenerate,
+                                  cudaStream_t st) {
     if (nops <= 0) return cudaSuccess;
-    svd_bwd_coeffs_kernel<<<dim3(256, nops), CT, 0, st>>>(d_desc, rel_broadening);
+    svd_bwd_coeffs_kernel<<<dim3(256, nops), CT, 0, st>>>(d_desc, rel_broadening, rel_degenerate);
     return cudaGetLastError();
 }
 

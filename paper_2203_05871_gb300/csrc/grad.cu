@@ -30,6 +30,7 @@ namespace mpdo {
 namespace {
 
 constexpr double kBroadening = 1e-12;   // delta = kBroadening * s_0^2 in the Lorentzian 1/(s_j^2 - s_i^2)
+constexpr double kDegenerate = 1e-10;   // singular values equal to this (relative) form a degenerate pair
 constexpr int kBwdGemms = 10;
 
 // bump allocator over device chunks (checkpoints of one forward run)
@@ -332,7 +333,7 @@ int run_bwd_chunk(mpdo_ctx* c, GradState* g, const std::vector<const TapeRec*>& 
     CU(launch_copy2d(g->d_bc, 2 * nops, max_pack, c->st));
     CU(gemm(0));
     CU(gemm(1));
-    CU(launch_svd_bwd_coeffs(g->d_bd, nops, kBroadening, c->st));
+    CU(launch_svd_bwd_coeffs(g->d_bd, nops, kBroadening, kDegenerate, c->st));
     CU(gemm(2));
     CU(gemm(3));
     CU(gemm(4));

@@ -194,7 +194,8 @@ struct BwdDesc {
     double* gpart;          // [parts][256] partial G-bar sums of this launch
     double* gacc;           // [256] G-bar of the op, accumulated over steps
 };
-cudaError_t launch_svd_bwd_coeffs(const BwdDesc* d_desc, int nops, double rel_broadening, cudaStream_t st);
+cudaError_t launch_svd_bwd_coeffs(const BwdDesc* d_desc, int nops, double rel_broadening, double rel_degenerate,
+                                  cudaStream_t st);
 cudaError_t launch_lambda_bwd(const BwdDesc* d_desc, int nops, int max_cl, cudaStream_t st);
 cudaError_t launch_gate_bwd(const BwdDesc* d_desc, int nops, int parts, cudaStream_t st);
 constexpr int kGateBwdParts = 32;
