@@ -19,6 +19,9 @@ the method has no exchange step between instances.
 ``--impl reference`` times the CPU oracle (plain C Jacobi, one thread) on a
 bounded sample: each step is one 1024 x 1024 gate application.
 ``--probe-peaks`` measures the FP64 / FP32 / TF32 GEMM rates with cuBLAS.
+``adjoint`` (``--adjoint-steps``, default 1): one gradient of the observables
+on the N=24 ring at chi = 256 (checkpointed forward, then recompute and
+backward), timed next to plain steps from the same state.
 """
 from __future__ import annotations
 
@@ -46,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--probe-peaks", action="store_true")
+    ap.add_argument("--adjoint-steps", type=int, default=1,
+                    help="Trotter steps of the timed gradient on the N=24 ring at chi=256 (0: skip)")
     return ap.parse_args()
 
 
@@ -276,6 +281,58 @@ def run_arm(args, precision, world, dist, local):
             "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
 
+def run_adjoint(args, local):
+    """One gradient (checkpointed forward + backward) of sum_i zbar_i <z_i> +
+    sum_{i<j} wbar_ij conn_ij on the N=24 ring (closing bond routed by swaps)
+    at chi_max = 256, mixed contractions with the FP64 SVD, next to the plain
+    forward steps of the same state."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2203_05871_gb300 import MIXED_TF32, Solver
+
+    K = args.adjoint_steps
+    wl = W.ring24_adjoint()
+    dims, tens = W.random_mpo_state(wl.n, 256, seed=2203058712 + 2, decay=DECAY)
+    stream = torch.cuda.Stream()
+    s = Solver(wl.n, batch=1, chi_cap=256, stream=stream, precision=MIXED_TF32)
+    s.build_gates(wl)
+    rng = np.random.default_rng(2203058712)
+    zb = rng.normal(size=(1, wl.n))
+    wb = np.triu(rng.normal(size=(1, wl.n, wl.n)), 1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    with ClockSampler(local) as clk:
+        s.set_state(0, dims, tens)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        s.step(K)
+        ev[1].record(stream)
+        s.set_state(0, dims, tens)
+        torch.cuda.synchronize()
+        ev[2].record(stream)
+        s.grad_forward(K)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        ev[4].record(stream)
+        g, L = s.grad_backward(zb, wb)
+        ev[5].record(stream)
+        torch.cuda.synchronize()
+    n_ops = s.op_counts()[0]
+    st = s.status()
+    s.close()
+    step_ms = ev[0].elapsed_time(ev[1])
+    fwd_ms = ev[2].elapsed_time(ev[3])
+    bwd_ms = ev[4].elapsed_time(ev[5])
+    return {"workload": "ring24_chi256 (N=24 ring, closing bond through swap gates, cutoff 1e-10, dt 0.05; "
+                        "seeded random MPO start at chi 256)",
+            "precision": "mixed contractions, FP64 SVD", "trotter_steps": K, "ops_per_step": n_ops,
+            "s_per_step_plain": step_ms / 1e3 / K, "s_per_step_grad_forward": fwd_ms / 1e3 / K,
+            "s_per_step_grad_backward": bwd_ms / 1e3 / K,
+            "gradient_over_plain": (fwd_ms + bwd_ms) / step_ms if step_ms > 0 else None,
+            "grad_finite": bool(np.all(np.isfinite(g))), "n_params": int(g.shape[1]),
+            "loss": float(L[0]), "chi_max_seen": int(st["chi"].max()), "clocks": clk.summary()}
+
+
 def main():
     args = parse()
     if args.probe_peaks:
@@ -346,6 +403,8 @@ def main():
                                                     if f["prof"]["jacobi_svd"]["svds"] else None),
                              "clocks": f["clocks"]}
         line["speedup_mixed_vs_fp64"] = f["ms"] / head["ms"]
+    if args.adjoint_steps > 0:
+        line["adjoint"] = run_adjoint(args, local)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args)
     if rank == 0:

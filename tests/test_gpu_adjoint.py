@@ -292,3 +292,43 @@ def test_grad_state_errors():
     assert e.value.code == -1
     g, L = s.grad_backward(np.ones((1, 4)), None)
     assert np.all(np.isfinite(g))
+
+
+def test_torch_autograd_function_matches_finite_differences():
+    """A nonlinear fitting loss through the torch.autograd.Function."""
+    torch = pytest.importorskip("torch")
+    from paper_2203_05871_gb300 import autograd as AG
+    wl = W.random_model(5, W.chain_bonds(5), 38, chi_max=8, cutoff=1e-10, dt=0.05)
+    steps = 3
+    s = solver_for(wl)
+    p = torch.tensor(AG.pack_params(wl), dtype=torch.float64, requires_grad=True)
+    target = torch.linspace(-0.5, 0.5, 5, dtype=torch.float64)[None]
+
+    def loss_of(z, C):
+        return ((z - target) ** 2).sum() + 0.5 * (C ** 2).sum()
+
+    z, C = AG.observables(p, s, wl, steps)
+    loss = loss_of(z, C)
+    loss.backward()
+    ranks = s.rank_log(steps)
+
+    def L(pp):
+        w = AG.with_params(wl, pp)
+        s.build_gates(w)
+        s.force_ranks(ranks)
+        s.step(steps)
+        s.force_ranks(None)
+        zz = torch.from_numpy(s.measure_1q(range(5), "Z"))
+        pairs = [(i, j) for i in range(5) for j in range(i + 1, 5)]
+        CC = torch.from_numpy(AG.connected_matrix(s.measure_2q(pairs, "ZZ", connected=True), 5))
+        return float(loss_of(zz, CC))
+
+    p0 = AG.pack_params(wl)
+    assert abs(L(p0) - float(loss)) < 1e-12
+    h = 1e-6
+    for k in [0, 7, 11, 16, 22, 27, 30, 33, 36]:
+        pp, pm = p0.copy(), p0.copy()
+        pp[0, k] += h
+        pm[0, k] -= h
+        fd = (L(pp) - L(pm)) / (2 * h)
+        assert abs(float(p.grad[0, k]) - fd) < 1e-6 * max(1.0, abs(fd)), (k, float(p.grad[0, k]), fd)
