@@ -64,11 +64,14 @@ DECAY = 0.045
 def make_workload(name):
     import workloads as W
     table = {"chain20_chi256": (256, DECAY), "chain20_chi256_flat": (256, 0.0),
-             "chain20_chi128": (128, DECAY), "chain20_chi64": (64, DECAY)}
+             "chain20_chi128": (128, DECAY), "chain20_chi64": (64, DECAY),
+             "chain10_chi256": (256, DECAY)}
     if name not in table:
         raise SystemExit(f"unknown workload {name}")
     chi, decay = table[name]
     wl = W.chain20_precision(chi_max=chi)
+    if name.startswith("chain10"):   # small case of the same model (profiling)
+        wl = W.uniform_model("chain10_chi256", 10, W.chain_bonds(10), chi_max=chi, cutoff=1e-10, dt=0.02)
     dims, tens = W.random_mpo_state(wl.n, chi, seed=2203058712 + 1, decay=decay)
     return wl, dims, tens, chi
 
