@@ -24,16 +24,17 @@
 // cs = 1/sqrt(1+t^2), sn = cs t;  w_p <- cs w_p - sn w_q, w_q <- sn w_p + cs w_q,
 // and then |w_p|^2 = a - t g, |w_q|^2 = b + t g (recomputed from the row when
 // the update loses more than 90% of the old value, and at every sweep start).
-// A pair is skipped when g^2 <= tol^2 a b (tol = sqrt(L) eps unless set): kept
-// rows are normalised into singular vectors, so they must be orthogonal
+// A pair is skipped when |g| <= tol sqrt(a b) (tol = sqrt(L) eps unless set):
+// kept rows are normalised into singular vectors, so they must be orthogonal
 // relative to their own norms.
 //
 // The same kernel, instantiated for float, is the preconditioning pass of the
 // mixed-precision SVD: it orthogonalises an FP32 copy of the rows (scaled to
 // unit mean square norm) and accumulates its rotations in U32; the FP64 pass
 // then starts from Q W with Q the FP64-orthogonalised U32 (see api.cu).
-// A row whose norm is at most eps * ||W||_F is numerically zero: it is set to
-// zero and never rotated (its direction is rounding noise).
+// A row whose norm is at most eps * ||W||_F (FP64 eps, in both passes) is
+// numerically zero: it is set to zero and never rotated (its direction is
+// rounding noise).
 #include <float.h>
 #include <mpdo.h>
 
@@ -138,7 +139,14 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         return 0;
     }
     const T g = row_dot(rp, rq, C.L, lane);
-    if (g == T(0) || g * g <= C.tol * C.tol * a * b) return 0;
+    // |g| <= tol sqrt(a b), written without squares of squares: in FP32, g^2
+    // and a b underflow for rows below ~1e-10 of the largest, and those pairs
+    // would pass as converged without ever being rotated
+    if constexpr (sizeof(T) == 4) {
+        if (g == T(0) || fabsf(g) <= C.tol * sqrtf(a) * sqrtf(b)) return 0;
+    } else {
+        if (g == T(0) || g * g <= C.tol * C.tol * a * b) return 0;   // no underflow in FP64's range
+    }
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
@@ -254,7 +262,10 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     if (threadIdx.x == 0) {
         double f = 0.0;
         for (int j = 0; j < c; ++j) f += __ldcg(d.snorm + j);
-        s_floor2 = (kF32 ? (double)FLT_EPSILON * FLT_EPSILON : DBL_EPSILON * DBL_EPSILON) * f;
+        // numerical zero of the FP64 data in both passes: the FP32 copy of a row
+        // far below eps32 ||W|| is still accurate relative to its own norm (the
+        // rows of R are graded), so the preconditioning pass must rotate it too
+        s_floor2 = DBL_EPSILON * DBL_EPSILON * f;
         s_scale = f > 0.0 ? sqrt((double)c / f) : 1.0;   // FP32 pass: rows of unit mean square norm
     }
     __syncthreads();
@@ -343,7 +354,9 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                 if (r == nbp - 2 && lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
                 if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             }
-            if (threadIdx.x == 0) s_conv = (ld_acquire(&sw[8 + sweep]) == 0u);
+            // FP32 pass: done when fewer than c/4 pairs still rotate (a few pairs
+            // sit at FP32's resolution forever; the FP64 pass finishes them)
+            if (threadIdx.x == 0) s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u));
             __syncthreads();
             conv = s_conv;
             used = sweep + 1;
