@@ -264,6 +264,19 @@ def run_arm(args, precision, world, dist, local):
             ms += e0.elapsed_time(e1)
     prof = s.profile_read(reset=True)
     s.profile(False)
+    # the same steps replayed as a captured CUDA graph (first call captures)
+    s.step(1, graph=True)
+    graph_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(1, graph=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        graph_ms += e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -280,7 +293,8 @@ def run_arm(args, precision, world, dist, local):
         s.measure_1q(range(wl.n), "Z")
         e2e_ms += (time.perf_counter() - t0) * 1e3
     s.close()
-    return {"wl": wl, "cap": cap, "n_ops": n_ops, "n_swaps": n_swaps, "ms": ms, "prof": prof, "status": st,
+    return {"wl": wl, "cap": cap, "n_ops": n_ops, "n_swaps": n_swaps, "ms": ms, "graph_ms": graph_ms, "prof": prof,
+            "status": st,
             "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
 
@@ -395,6 +409,8 @@ def main():
                      "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
                              "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
                              "MEASURED_PEAKS.json)"},
+        "graph_step": {"ms_per_step": head["graph_ms"] / args.steps,
+                       "note": "same steps replayed from one captured CUDA graph (device-side planning)"},
         "clocks": head["clocks"],
         "status": int(head["status"]["status"][0]), "chi_max_seen": int(head["status"]["chi"].max()),
     }

@@ -115,6 +115,14 @@ int mpdo_build_gates(mpdo_ctx *ctx, const mpdo_model *model, double dt);
  * instances are still advanced), ESTATE before mpdo_build_gates. */
 int mpdo_trotter_step(mpdo_ctx *ctx, int n_steps);
 
+/* mpdo_trotter_step with the step captured into a CUDA graph: the first call
+ * after mpdo_build_gates captures one step (planner kernels read the bond
+ * dimensions on the device and size every launch there, so nothing returns
+ * to the host inside a step) and every call replays it n_steps times, then
+ * synchronises once.  Same results, rank log and status errors as
+ * mpdo_trotter_step; kernel profiling is not collected; EINVAL while forced
+ * ranks are set; ECAPACITY if a chunk holds more ops than co-resident CTAs. */
+int mpdo_trotter_step_graph(mpdo_ctx *ctx, int n_steps);
 /* <sigma^comp_q> / tr rho for each q in qubits[nq] and each instance
  * (Eq. (mu)); comp in 'X','Y','Z','I'.  out is [B][nq] doubles, a host
  * pointer (out_on_device = 0; the call synchronises) or a device pointer. */

@@ -56,6 +56,8 @@ void free_all(mpdo_ctx* c) {
         if (e) cudaEventDestroy(e);
     if (c->grad) grad_free(c->grad);
     c->grad = nullptr;
+    if (c->graph) graph_free(c->graph);
+    c->graph = nullptr;
 }
 
 int release_slots(mpdo_ctx* c) {
@@ -154,60 +156,70 @@ int check_status_code(mpdo_ctx* c) {
     return MPDO_OK;
 }
 
+void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
+    const int N = c->N, cap = c->cap, ld = c->ld;
+    const size_t mat = (size_t)ld * ld;
+    const Op& op = c->layers[it.layer][it.idx];
+    const int b = it.b, p = op.p;
+    const int* dm = &c->h_dims[(size_t)b * (N + 1)];
+    d = OpDesc{};
+    d.b = b;
+    d.op = c->layer_op0[it.layer] + it.idx;
+    d.p = p;
+    d.cl = dm[p];
+    d.cm = dm[p + 1];
+    d.cr = dm[p + 2];
+    d.m = 4 * d.cl;
+    d.n = 4 * d.cr;
+    d.transposed = 0;                 // the QR step leaves min(m, n) rows of length n
+    d.c = std::min(d.m, d.n);
+    d.L = d.n;
+    d.chi_max = c->chi_max[b];
+    d.cutoff = c->cutoff[b];
+    d.G = c->d_gates + ((size_t)b * c->n_ops + d.op) * 256;
+    d.A = site(c, b, p);
+    d.B = site(c, b, p + 1);
+    d.lam_left = p > 0 ? c->d_lam + ((size_t)b * N + (p - 1)) * cap : nullptr;
+    d.lam_out = c->d_lam + ((size_t)b * N + p) * cap;
+    d.thetap = c->d_thetap + (size_t)s * mat;
+    d.W = c->d_W + (size_t)s * mat;
+    d.Z = nullptr;
+    d.Acm = c->d_Z + (size_t)s * mat;
+    d.Yk = c->d_Yk + (size_t)s * cap * ld;
+    d.snorm = c->d_snorm + (size_t)s * 2 * ld;
+    d.k_out = c->d_dims + (size_t)b * (N + 1) + p + 1;
+    d.status = c->d_status + b;
+    d.max_disc = c->d_maxdisc + b;
+    d.rank_log = nullptr;
+    d.jb = jacobi_block_rows(d.L, d.c, 8);
+    d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
+    d.sweeps_out = c->d_sweeps + s;
+    d.forced_k = 0;
+    d.tape_V = nullptr;
+    d.tape_s = nullptr;
+    d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
+    d.W32 = c->mixed ? c->d_W32 + (size_t)s * mat : nullptr;
+    d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
+    d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
+    d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
+    d.Zinit = nullptr;
+}
+
 int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,
               bool log_ranks) {
     const int nops = (int)items.size();
     const int N = c->N, cap = c->cap, ld = c->ld;
-    const size_t mat = (size_t)ld * ld;
     std::vector<double> work(nops), qwork(nops);
     for (int s = 0; s < nops; ++s) {
         const Item& it = items[s];
-        const Op& op = c->layers[it.layer][it.idx];
-        const int b = it.b, p = op.p;
-        const int* dm = &c->h_dims[(size_t)b * (N + 1)];
         OpDesc& d = c->h_desc[s];
-        d.b = b;
-        d.op = c->layer_op0[it.layer] + it.idx;
-        d.cl = dm[p];
-        d.cm = dm[p + 1];
-        d.cr = dm[p + 2];
-        d.m = 4 * d.cl;
-        d.n = 4 * d.cr;
-        d.transposed = 0;                 // the QR step leaves min(m, n) rows of length n
-        d.c = std::min(d.m, d.n);
-        d.L = d.n;
-        d.chi_max = c->chi_max[b];
-        d.cutoff = c->cutoff[b];
-        d.G = c->d_gates + ((size_t)b * c->n_ops + d.op) * 256;
-        d.A = site(c, b, p);
-        d.B = site(c, b, p + 1);
-        d.lam_left = p > 0 ? c->d_lam + ((size_t)b * N + (p - 1)) * cap : nullptr;
-        d.lam_out = c->d_lam + ((size_t)b * N + p) * cap;
-        d.thetap = c->d_thetap + (size_t)s * mat;
-        d.W = c->d_W + (size_t)s * mat;
-        d.Z = nullptr;
-        d.Acm = c->d_Z + (size_t)s * mat;
-        d.Yk = c->d_Yk + (size_t)s * cap * ld;
-        d.snorm = c->d_snorm + (size_t)s * 2 * ld;
-        d.k_out = c->d_dims + (size_t)b * (N + 1) + p + 1;
-        d.status = c->d_status + b;
-        d.max_disc = c->d_maxdisc + b;
-        d.rank_log = nullptr;
-        d.jb = jacobi_block_rows(d.L, d.c, 8);
-        d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
-        d.sweeps_out = c->d_sweeps + s;
+        fill_desc(c, it, s, d);
         int fk = forced ? forced[s] : 0;
         if (!forced && step < c->forced_steps)
-            fk = c->forced[((size_t)b * c->forced_steps + step) * c->n_ops + d.op];
+            fk = c->forced[((size_t)d.b * c->forced_steps + step) * c->n_ops + d.op];
         d.forced_k = fk;
         d.tape_V = tape ? tape[s].V : nullptr;
         d.tape_s = tape ? tape[s].s : nullptr;
-        d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
-        d.W32 = c->mixed ? c->d_W32 + (size_t)s * mat : nullptr;
-        d.U32 = c->mixed ? c->d_U32 + (size_t)s * mat : nullptr;
-        d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
-        d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
-        d.Zinit = nullptr;
         work[s] = (double)d.c * d.c * (double)d.L;
         qwork[s] = (double)d.m * d.n * d.c;
     }
@@ -682,6 +694,7 @@ int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
     CU(cudaStreamSynchronize(c->st));
     c->built = true;
     ++c->gen;
+    ++c->layout;
     c->forced.clear();
     c->forced_steps = 0;
     return MPDO_OK;

@@ -51,6 +51,8 @@ struct TapeSlot {
 
 struct GradState;   // adjoint buffers (grad.cu)
 void grad_free(GradState* g);
+struct GraphState;  // captured step (graph.cu)
+void graph_free(GraphState* g);
 
 }  // namespace mpdo
 
@@ -112,6 +114,8 @@ struct mpdo_ctx {
     // adjoint
     mpdo::GradState* grad = nullptr;
     long long gen = 0;            // bumped whenever the state changes (step, set_state, build_gates)
+    long long layout = 0;         // bumped whenever the op list or the workspaces change (build_gates)
+    mpdo::GraphState* graph = nullptr;
     // profiling
     bool prof = false;
     cudaEvent_t ev[2 * mpdo::kProfKinds] = {};
@@ -141,6 +145,10 @@ struct ProfScope {
     }
 };
 void prof_collect(mpdo_ctx* c, int k, double flops);
+
+// Descriptor of item `it` in workspace slot s, with the bond dimensions of
+// c->h_dims (forced rank and tape cleared).
+void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d);
 
 // One chunk of (instance, op) items of a layer: merge + gate, QR, Jacobi SVD,
 // truncate, reconstruct.  forced (per item, or nullptr) imposes ranks; tape

@@ -39,6 +39,7 @@ std::string build_schedule(int n, const std::vector<int>& bi, const std::vector<
 struct OpDesc {
     int b;             // instance
     int op;            // op index within the step (for the rank log)
+    int p;             // left path position
     int cl, cm, cr;    // bond dims chi_{p-1}, chi_p, chi_{p+1}
     int m, n;          // 4*cl, 4*cr
     int transposed;    // 1: Jacobi rows carry a c x c accumulator Z (unused since the QR step)
@@ -95,8 +96,22 @@ struct JacobiPlan {
     int max_resident;    // co-resident capacity
 };
 int jacobi_threads();
-int jacobi_block_rows(int rowlen, int c, int elem_bytes);   // rows per block for rows of length rowlen
-int jacobi_pairs_per_round(int c, int b);      // block pairs per tournament round
+constexpr int kJacobiRowBytes = 128 * 1024;   // shared memory for the two row blocks of a pair
+constexpr int kJacobiMaxB = 32;               // rows per block at most
+constexpr int kQrWarps = 8;                   // warps per QR CTA
+// rows per block for rows of length rowlen (elem_bytes each): two blocks fit the
+// shared-memory budget, and there are at least two blocks when c > 1
+__host__ __device__ inline int jacobi_block_rows(int rowlen, int c, int elem_bytes) {
+    int b = kJacobiMaxB;
+    while (b > 1 && (size_t)2 * b * rowlen * elem_bytes > (size_t)kJacobiRowBytes) b >>= 1;
+    while (b > 1 && b >= c) b >>= 1;
+    return b;
+}
+// block pairs per tournament round
+__host__ __device__ inline int jacobi_pairs_per_round(int c, int b) {
+    const int nb = (c + b - 1) / b;
+    return (nb + (nb & 1)) / 2;
+}
 cudaError_t jacobi_max_resident(int* blocks);
 // d_cta_op[grid]: op index of each CTA; d_cta_rank[grid]: rank within its op;
 // d_group[nops]: CTAs per op.  d_sync: per-op counters (zeroed by the caller,

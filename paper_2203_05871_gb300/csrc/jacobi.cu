@@ -47,8 +47,8 @@ namespace {
 
 constexpr int JW = 8;             // warps per CTA
 constexpr int JT = JW * 32;
-constexpr int kRowBytes = 128 * 1024;                  // two blocks of rows in shared memory
-constexpr int kMaxB = 32;
+constexpr int kRowBytes = kJacobiRowBytes;             // two blocks of rows in shared memory
+constexpr int kMaxB = kJacobiMaxB;
 constexpr int kSmemBytes = kRowBytes + 4 * kMaxB * 8;  // rows + norms (2b) + row ids
 
 __device__ __forceinline__ int tour_player(int x, int step, int cp) {
@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kF32 = sizeof(T) == 4;
     const int op = cta_op[blockIdx.x];
+    if (op < 0) return;   // a CTA the plan left unused (graph step)
     const int g = cta_rank[blockIdx.x];
     const int G = group[op];
     const OpDesc& d = descs[op];
@@ -380,17 +381,6 @@ timeout:
 int jacobi_threads() { return JT; }
 size_t jacobi_sync_words_per_op() { return kSyncWords; }
 
-int jacobi_block_rows(int rowlen, int c, int elem_bytes) {
-    int b = kMaxB;
-    while (b > 1 && (size_t)2 * b * rowlen * elem_bytes > (size_t)kRowBytes) b >>= 1;
-    while (b > 1 && b >= c) b >>= 1;   // at least two blocks when c > 1
-    return b;
-}
-
-int jacobi_pairs_per_round(int c, int b) {
-    const int nb = (c + b - 1) / b;
-    return (nb + (nb & 1)) / 2;
-}
 
 cudaError_t jacobi_max_resident(int* blocks) {
     int dev = 0, sms = 0, per64 = 0, per32 = 0;

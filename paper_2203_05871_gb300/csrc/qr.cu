@@ -32,7 +32,7 @@ namespace mpdo {
 
 namespace {
 
-constexpr int QW = 8;   // warps per CTA
+constexpr int QW = kQrWarps;   // warps per CTA
 constexpr int QT = QW * 32;
 constexpr int kMaxRowsQR = 4 * kMaxChi;
 
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(QT, 1) qr_kernel(const OpDesc* descs, const in
                                                    const int* group, unsigned* sync, unsigned long long timeout_ns,
                                                    int ld) {
     const int op = cta_op[blockIdx.x];
+    if (op < 0) return;   // a CTA the plan left unused (graph step)
     const int g = cta_rank[blockIdx.x];
     const int G = group[op];
     const OpDesc& d = descs[op];

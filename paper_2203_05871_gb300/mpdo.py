@@ -66,6 +66,7 @@ def load_library(path: str = LIB_PATH):
         "mpdo_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.POINTER(Config), vp]),
         "mpdo_build_gates": (ctypes.c_int, [vp, ctypes.POINTER(Model), ctypes.c_double]),
         "mpdo_trotter_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mpdo_trotter_step_graph": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_measure_1q": (ctypes.c_int, [vp, _ip, ctypes.c_int, ctypes.c_char, vp, ctypes.c_int]),
         "mpdo_measure_2q": (ctypes.c_int, [vp, _ip, ctypes.c_int, ctypes.c_char_p, ctypes.c_int, vp,
                                            ctypes.c_int]),
@@ -100,7 +101,8 @@ def load_library(path: str = LIB_PATH):
 
 def exported_symbols() -> list[str]:
     """Names declared in include/mpdo.h (for the export test)."""
-    return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_measure_1q",
+    return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_trotter_step_graph",
+            "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
             "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
@@ -219,8 +221,10 @@ class Solver:
         _check(self._lib.mpdo_build_gates(self._h, ctypes.byref(m), float(wl.dt if dt is None else dt)))
         self._n_bonds = len(wl.bonds)
 
-    def step(self, n_steps: int = 1, check: bool = True):
-        rc = self._lib.mpdo_trotter_step(self._h, int(n_steps))
+    def step(self, n_steps: int = 1, check: bool = True, graph: bool = False):
+        """n_steps Trotter steps (graph=True: replay the step captured as a CUDA graph)."""
+        fn = self._lib.mpdo_trotter_step_graph if graph else self._lib.mpdo_trotter_step
+        rc = fn(self._h, int(n_steps))
         if check:
             _check(rc)
         return rc

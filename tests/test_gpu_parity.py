@@ -290,3 +290,35 @@ def test_errors_are_codes_not_crashes():
     with pytest.raises(MpdoError):
         s.measure_2q([(1, 1)])
     s.step(1)
+
+
+# ---------------------------------------------------------------------------
+# the step captured as a CUDA graph
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_step_equals_plain_step(precision):
+    """Device-planned, graph-replayed steps reproduce the host-planned steps
+    exactly (same ranks, same tensors): chain8 for 40 steps, and a batch of
+    three instances with uneven chi_max on a swap-routed ring."""
+    from paper_2203_05871_gb300 import FP64, MIXED_TF32
+    prec = FP64 if precision == "fp64" else MIXED_TF32
+    cases = [(W.chain8_fp64(), 40, None),
+             (W.random_model(6, W.ring_bonds(6), 71, batch=3, chi_max=16, cutoff=1e-11), 5, [4, 8, 16])]
+    for wl, steps, chis in cases:
+        if chis:
+            wl.chi_max[:] = chis
+        a = solver_for(wl, precision=prec)
+        b = solver_for(wl, precision=prec)
+        a.step(steps)
+        b.step(steps, graph=True)
+        assert np.array_equal(a.rank_log(steps), b.rank_log(steps))
+        for inst in range(wl.batch):
+            da, ta = a.get_state(inst)
+            db, tb = b.get_state(inst)
+            assert da == db
+            for x, y in zip(ta, tb):
+                assert np.array_equal(x, y)
+        # a second replay continues from the replayed state
+        a.step(2)
+        b.step(2, graph=True)
+        assert np.abs(a.measure_1q(range(wl.n), "Z") - b.measure_1q(range(wl.n), "Z")).max() == 0.0
