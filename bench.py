@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--probe-peaks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default Jacobi block rule")
     ap.add_argument("--adjoint-steps", type=int, default=1,
                     help="Trotter steps of the timed gradient on the N=24 ring at chi=256 (0: skip)")
     return ap.parse_args()
@@ -62,7 +63,15 @@ DECAY = 0.045
 
 
 def make_workload(name):
+    """(workload, [(dims, tensors)] per instance, chi_cap)."""
     import workloads as W
+    if name == "batch64_chain16":
+        # 64 independent N=16 chains, chi_max drawn from {32, 64, 128, 256} per
+        # instance, each started at its own saturated chi (seeded random MPO)
+        wl = W.batch64_chain16()
+        states = [W.random_mpo_state(wl.n, int(wl.chi_max[b]), seed=2203058712 + 100 + b, decay=DECAY)
+                  for b in range(wl.batch)]
+        return wl, states, 256
     table = {"chain20_chi256": (256, DECAY), "chain20_chi256_flat": (256, 0.0),
              "chain20_chi128": (128, DECAY), "chain20_chi64": (64, DECAY),
              "chain10_chi256": (256, DECAY)}
@@ -72,8 +81,7 @@ def make_workload(name):
     wl = W.chain20_precision(chi_max=chi)
     if name.startswith("chain10"):   # small case of the same model (profiling)
         wl = W.uniform_model("chain10_chi256", 10, W.chain_bonds(10), chi_max=chi, cutoff=1e-10, dt=0.02)
-    dims, tens = W.random_mpo_state(wl.n, chi, seed=2203058712 + 1, decay=decay)
-    return wl, dims, tens, chi
+    return wl, [W.random_mpo_state(wl.n, chi, seed=2203058712 + 1, decay=decay)], chi
 
 
 class ClockSampler:
@@ -164,8 +172,10 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl, dims, tens, cap = make_workload(args.workload)
-    times, what = oracle_sample(wl, dims, tens, args.steps, min(args.warmup, 1))
+    wl, states, cap = make_workload(args.workload)
+    b = next(i for i in range(wl.batch) if int(wl.chi_max[i]) == cap)   # an instance at full chi
+    dims, tens = states[b]
+    times, what = oracle_sample(wl.instance(b), dims, tens, args.steps, min(args.warmup, 1))
     v = len(times) / sum(times)
     line = {"impl": "reference", "metric": "gate_applications_per_sec", "value": v,
             "unit": "gate-applications/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
@@ -236,12 +246,20 @@ def run_arm(args, precision, world, dist, local):
     import torch
     from paper_2203_05871_gb300 import FP64, MIXED_TF32, Solver
 
-    wl, dims, tens, cap = make_workload(args.workload)
+    wl, states, cap = make_workload(args.workload)
     stream = torch.cuda.Stream()
-    s = Solver(wl.n, batch=1, chi_cap=cap, stream=stream, precision=FP64 if precision == "fp64" else MIXED_TF32)
+    s = Solver(wl.n, batch=wl.batch, chi_cap=cap, stream=stream,
+               precision=FP64 if precision == "fp64" else MIXED_TF32)
     s.build_gates(wl)
-    s.set_state(0, dims, tens)
+    tuned = None
+    if not args.no_autotune:
+        from paper_2203_05871_gb300.mpdo import saturated_classes
+        cls = saturated_classes(wl.n, cap)
+        tuned = {f"{a}x{b}": [int(x) for x in blk] for (a, b), blk in zip(cls, s.autotune(cls))}
+    for b, (dims, tens) in enumerate(states):
+        s.set_state(b, dims, tens)
     n_ops, n_swaps, _ = s.op_counts()
+    n_ops_all = n_ops * wl.batch
     for _ in range(args.warmup):
         s.step(1)
     torch.cuda.synchronize()
@@ -283,18 +301,20 @@ def run_arm(args, precision, world, dist, local):
         ms = float(t.item())
     st = s.status()
     # end to end through the C ABI from host buffers (state in, observables out)
-    flat_bytes = sum(int(np.asarray(t).size) for t in tens) * 8
+    flat_bytes = sum(int(np.asarray(t).size) for (_, tens) in states for t in tens) * 8
     e2e_ms = 0.0
     for _ in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s.set_state(0, dims, tens)
+        for b, (dims, tens) in enumerate(states):
+            s.set_state(b, dims, tens)
         s.step(1)
         s.measure_1q(range(wl.n), "Z")
         e2e_ms += (time.perf_counter() - t0) * 1e3
     s.close()
-    return {"wl": wl, "cap": cap, "n_ops": n_ops, "n_swaps": n_swaps, "ms": ms, "graph_ms": graph_ms, "prof": prof,
-            "status": st,
+    return {"wl": wl, "cap": cap, "n_ops": n_ops_all, "n_swaps": n_swaps, "ms": ms, "graph_ms": graph_ms,
+            "prof": prof,
+            "status": st, "tuned": tuned,
             "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
 
@@ -390,13 +410,14 @@ def main():
         "s_per_trotter_step": ms_per_step / 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "n_qubits": wl.n, "chi_max": cap, "cutoff": float(wl.cutoff[0]),
+        "config": {"workload": args.workload, "n_qubits": wl.n, "batch": wl.batch, "chi_max": cap,
+                   "cutoff": float(wl.cutoff[0]),
                    "dt": wl.dt, "ops_per_step": n_ops, "swaps_per_step": head["n_swaps"], "precision": hp,
                    "parallelism": f"replicas{world}", "l2": "flushed (256 MB write) between timed steps",
                    "start": "seeded random MPO at chi_max, Schmidt grading exp(-%.3f r)" % (
                        DECAY if "flat" not in args.workload else 0.0)},
         "e2e": {"value": e2e_value, "unit": "gate-applications/s", "h2d_bytes_per_step": head["flat_bytes"],
-                "d2h_bytes_per_step": wl.n * 8},
+                "d2h_bytes_per_step": wl.n * wl.batch * 8},
         "gpu_launches": launches,
         "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
                     for k, v in prof.items() if v["launches"]},
@@ -409,6 +430,8 @@ def main():
                      "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
                              "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
                              "MEASURED_PEAKS.json)"},
+        "autotune": {"jacobi_rows_per_block": head["tuned"],
+                     "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},
         "graph_step": {"ms_per_step": head["graph_ms"] / args.steps,
                        "note": "same steps replayed from one captured CUDA graph (device-side planning)"},
         "clocks": head["clocks"],

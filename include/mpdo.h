@@ -167,6 +167,16 @@ int mpdo_rank_log(mpdo_ctx *ctx, int *k, long long cap);
  * n_steps <= 0 clears.  mpdo_build_gates clears as well.  Used for finite-
  * difference gradients, which need the ranks held fixed.  EINVAL, ESTATE. */
 int mpdo_force_ranks(mpdo_ctx *ctx, const int *k, int n_steps);
+/* Autotune the Jacobi SVD's rows per block for each bond-dimension class
+ * (chi_l, chi_r) in classes[n_classes][2] (each in [1, chi_cap]): for every
+ * candidate block size that fits shared memory, the Jacobi launch is timed on
+ * seeded graded matrices of the class's shape, one per op in flight (the
+ * largest layer), and the fastest is kept (FP64 pass, and the FP32 pass of the
+ * mixed path).  Later steps (plain and graph) use the table; classes not tuned
+ * keep the default rule (largest block that fits).  chosen (host, may be NULL)
+ * receives [n_classes][2] = (FP64 block, FP32 block or 0).  Uses the per-op
+ * workspaces only (the state is untouched); synchronises.  EINVAL, ESTATE, ECUDA. */
+int mpdo_autotune(mpdo_ctx *ctx, const int *classes, int n_classes, int *chosen);
 /* Copy instance b's gate matrices out: [n_ops][16][16] row-major doubles in
  * step order (swaps included), host memory, cap = capacity in doubles. */
 int mpdo_gates(mpdo_ctx *ctx, int b, double *out, long long cap);

@@ -47,9 +47,9 @@ namespace mpdo {
 
 void free_all(mpdo_ctx* c) {
     release_slots(c);
-    void* ptrs[] = {c->d_sites, c->d_lam,  c->d_dims, c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
-                    c->d_gates, c->d_specs, c->d_envL, c->d_envR,  c->d_full,    c->d_one_a, c->d_one_b,
-                    c->d_out,   c->d_q,     c->d_pairs, c->d_need};
+    void* ptrs[] = {c->d_sites, c->d_lam,  c->d_dims,  c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
+                    c->d_gates, c->d_specs, c->d_envL,  c->d_envR,   c->d_full,    c->d_one_a, c->d_one_b,
+                    c->d_out,   c->d_q,     c->d_pairs, c->d_need,   c->d_jb_table};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -156,6 +156,43 @@ int check_status_code(mpdo_ctx* c) {
     return MPDO_OK;
 }
 
+int plan_jacobi(mpdo_ctx* c, const OpDesc* h, int nops, bool fp32, int* hbase, int& total) {
+    const int R = c->jacobi_resident;
+    std::vector<double> work(nops);
+    double wsum = 0.0;
+    for (int s = 0; s < nops; ++s) {
+        work[s] = (double)h[s].c * h[s].c * (double)h[s].L;
+        wsum += work[s];
+    }
+    std::vector<int> G(nops, 1);
+    total = 0;
+    for (int s = 0; s < nops; ++s) {
+        const OpDesc& d = h[s];
+        const int pairs = jacobi_pairs_per_round(d.c, fp32 ? d.jb32 : d.jb);
+        int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
+        g = std::max(1, std::min(pairs, g));
+        const int passes = (pairs + g - 1) / g;      // block pairs per CTA per round
+        g = (pairs + passes - 1) / passes;           // fewest CTAs with that many passes
+        G[s] = g;
+        total += g;
+    }
+    while (total > R) {   // trim the largest groups until everything is co-resident
+        int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
+        if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident Jacobi CTAs");
+        G[arg]--;
+        total--;
+    }
+    int t = 0;
+    for (int s = 0; s < nops; ++s) {
+        hbase[2 * total + s] = G[s];
+        for (int g = 0; g < G[s]; ++g, ++t) {
+            hbase[t] = s;
+            hbase[total + t] = g;
+        }
+    }
+    return MPDO_OK;
+}
+
 void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     const int N = c->N, cap = c->cap, ld = c->ld;
     const size_t mat = (size_t)ld * ld;
@@ -191,8 +228,8 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.status = c->d_status + b;
     d.max_disc = c->d_maxdisc + b;
     d.rank_log = nullptr;
-    d.jb = jacobi_block_rows(d.L, d.c, 8);
-    d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
+    d.jb = tuned_block_rows(c, d.cl, d.cr, false, jacobi_block_rows(d.L, d.c, 8));
+    d.jb32 = tuned_block_rows(c, d.cl, d.cr, true, jacobi_block_rows(d.L + d.c, d.c, 4));
     d.sweeps_out = c->d_sweeps + s;
     d.forced_k = 0;
     d.tape_V = nullptr;
@@ -272,36 +309,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
     // Jacobi launch plan: share the co-resident CTAs among the ops in
     // proportion to their work; h_cta/d_cta hold [op of each CTA | rank | CTAs per op]
     auto plan = [&](bool fp32, int* hbase, int& total) -> int {
-        const int R = c->jacobi_resident;
-        double wsum = 0.0;
-        for (double w : work) wsum += w;
-        std::vector<int> G(nops, 1);
-        total = 0;
-        for (int s = 0; s < nops; ++s) {
-            const OpDesc& d = c->h_desc[s];
-            const int pairs = jacobi_pairs_per_round(d.c, fp32 ? d.jb32 : d.jb);
-            int g = (int)std::floor((double)R * work[s] / std::max(wsum, 1.0));
-            g = std::max(1, std::min(pairs, g));
-            const int passes = (pairs + g - 1) / g;      // block pairs per CTA per round
-            g = (pairs + passes - 1) / passes;           // fewest CTAs with that many passes
-            G[s] = g;
-            total += g;
-        }
-        while (total > R) {   // trim the largest groups until everything is co-resident
-            int arg = (int)(std::max_element(G.begin(), G.end()) - G.begin());
-            if (G[arg] <= 1) return fail(MPDO_ECAPACITY, "more ops in flight than co-resident Jacobi CTAs");
-            G[arg]--;
-            total--;
-        }
-        int t = 0;
-        for (int s = 0; s < nops; ++s) {
-            hbase[2 * total + s] = G[s];
-            for (int g = 0; g < G[s]; ++g, ++t) {
-                hbase[t] = s;
-                hbase[total + t] = g;
-            }
-        }
-        return MPDO_OK;
+        return plan_jacobi(c, c->h_desc, nops, fp32, hbase, total);
     };
     auto run_jacobi = [&](bool fp32, int slot) -> int {
         int total = 0;

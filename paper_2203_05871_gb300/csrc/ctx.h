@@ -116,6 +116,9 @@ struct mpdo_ctx {
     long long gen = 0;            // bumped whenever the state changes (step, set_state, build_gates)
     long long layout = 0;         // bumped whenever the op list or the workspaces change (build_gates)
     mpdo::GraphState* graph = nullptr;
+    // autotuned Jacobi rows per block: [(chi_l * (cap+1) + chi_r) * 2 + fp32], 0 = the default rule
+    std::vector<int> jb_table;
+    int* d_jb_table = nullptr;
     // profiling
     bool prof = false;
     cudaEvent_t ev[2 * mpdo::kProfKinds] = {};
@@ -145,6 +148,17 @@ struct ProfScope {
     }
 };
 void prof_collect(mpdo_ctx* c, int k, double flops);
+
+// Jacobi rows per block of a (chi_l, chi_r) class: the autotuned value, else dflt.
+inline int tuned_block_rows(const mpdo_ctx* c, int cl, int cr, bool fp32, int dflt) {
+    if (c->jb_table.empty() || cl > c->cap || cr > c->cap) return dflt;
+    const int v = c->jb_table[((size_t)cl * (c->cap + 1) + cr) * 2 + (fp32 ? 1 : 0)];
+    return v > 0 ? v : dflt;
+}
+
+// Co-resident CTA plan of the Jacobi launch over h[0..nops): hbase receives
+// [op of each CTA | rank | CTAs per op], total the number of CTAs.
+int plan_jacobi(mpdo_ctx* c, const OpDesc* h, int nops, bool fp32, int* hbase, int& total);
 
 // Descriptor of item `it` in workspace slot s, with the bond dimensions of
 // c->h_dims (forced rank and tape cleared).

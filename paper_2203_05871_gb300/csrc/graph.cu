@@ -68,7 +68,8 @@ constexpr int kMaxChunk = 1024;
 
 __global__ void __launch_bounds__(256) plan_chunk_kernel(OpDesc* descs, int nops, const int* dims, int N, int Rj,
                                                          int Rq, int* cta64, int* cta32, int* ctaqr, GemmDesc* gemm,
-                                                         int ld, int mixed, int* error) {
+                                                         int ld, int mixed, const int* jb_table, int chi_cap,
+                                                         int* error) {
     __shared__ double work[kMaxChunk];
     __shared__ int cap[kMaxChunk];
     for (int s = threadIdx.x; s < nops; s += blockDim.x) {
@@ -83,6 +84,11 @@ __global__ void __launch_bounds__(256) plan_chunk_kernel(OpDesc* descs, int nops
         d.L = d.n;
         d.jb = jacobi_block_rows(d.L, d.c, 8);
         d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
+        if (jb_table) {   // autotuned rows per block of this (chi_l, chi_r) class
+            const int* t = jb_table + ((size_t)d.cl * (chi_cap + 1) + d.cr) * 2;
+            if (t[0] > 0) d.jb = t[0];
+            if (t[1] > 0) d.jb32 = t[1];
+        }
         if (mixed) {
             gemm[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0};
             gemm[nops + s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0, 0};
@@ -168,7 +174,8 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
         for (auto& ch : L) {
             const int nops = ch.nops;
             plan_chunk_kernel<<<1, 256, 0, st>>>(ch.d_desc, nops, c->d_dims, c->N, g->Rj, g->Rq, ch.d_cta64,
-                                                 ch.d_cta32, ch.d_ctaqr, ch.d_gemm, ld, c->mixed ? 1 : 0, g->d_error);
+                                                 ch.d_cta32, ch.d_ctaqr, ch.d_gemm, ld, c->mixed ? 1 : 0,
+                                                 c->d_jb_table, cap, g->d_error);
             CU(cudaGetLastError());
             CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, st));
             if (c->mixed)

@@ -85,6 +85,7 @@ def load_library(path: str = LIB_PATH):
         "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
+        "mpdo_autotune": (ctypes.c_int, [vp, _ip, ctypes.c_int, _ip]),
         "mpdo_grad_forward": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_grad_backward": (ctypes.c_int, [vp, _dp, _dp, _dp, _dp]),
         "mpdo_grad": (ctypes.c_int, [vp, ctypes.c_int, _dp, _dp, _dp, _dp]),
@@ -104,7 +105,7 @@ def exported_symbols() -> list[str]:
     return ["mpdo_config_default", "mpdo_init", "mpdo_build_gates", "mpdo_trotter_step", "mpdo_trotter_step_graph",
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
-            "mpdo_rank_log", "mpdo_force_ranks", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
+            "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
             "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
@@ -350,3 +351,18 @@ class Solver:
                                             None if wb is None else _ptr(wb, ctypes.c_double),
                                             _ptr(g, ctypes.c_double), _ptr(loss, ctypes.c_double)))
         return g, loss
+
+    def autotune(self, classes):
+        """Tune the Jacobi block size for each (chi_l, chi_r) in classes; returns
+        [n, 2] (FP64 block, FP32 block or 0)."""
+        cl = _as(classes, np.int32).reshape(-1, 2)
+        out = np.zeros_like(cl)
+        _check(self._lib.mpdo_autotune(self._h, _ptr(cl, ctypes.c_int), len(cl), _ptr(out, ctypes.c_int)))
+        return out
+
+
+def saturated_classes(n_qubits: int, chi_max: int):
+    """(chi_l, chi_r) of the ops of an n-qubit path once every bond is at its
+    largest dimension min(4^(p+1), 4^(n-1-p), chi_max)."""
+    d = [1] + [min(4 ** (p + 1), 4 ** (n_qubits - 1 - p), chi_max) for p in range(n_qubits - 1)] + [1]
+    return sorted({(d[p], d[p + 2]) for p in range(n_qubits - 1)})

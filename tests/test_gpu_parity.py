@@ -322,3 +322,52 @@ def test_graph_step_equals_plain_step(precision):
         a.step(2)
         b.step(2, graph=True)
         assert np.abs(a.measure_1q(range(wl.n), "Z") - b.measure_1q(range(wl.n), "Z")).max() == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_blocks_keep_parity(precision):
+    """The autotuner picks a power-of-two block per (chi_l, chi_r) class; steps
+    with the tuned table still match the oracle, and the graph step still
+    equals the host-planned step."""
+    from paper_2203_05871_gb300 import FP64, MIXED_TF32
+    from paper_2203_05871_gb300.mpdo import saturated_classes
+    prec = FP64 if precision == "fp64" else MIXED_TF32
+    wl = W.chain8_fp64()
+    s = solver_for(wl, precision=prec)
+    cls = saturated_classes(wl.n, int(wl.chi_max[0]))
+    ch = s.autotune(cls)
+    for (b64, b32) in ch:
+        assert b64 >= 1 and b64 & (b64 - 1) == 0
+        assert (b32 == 0) if precision == "fp64" else (b32 >= 1 and b32 & (b32 - 1) == 0)
+    s.build_gates(wl)
+    compare_to_oracle(wl, 12, s, tol=TOL if precision == "fp64" else TOL_MIXED)
+    g = solver_for(wl, precision=prec)
+    g.autotune(cls)
+    g.build_gates(wl)
+    s.build_gates(wl)
+    s.step(6)
+    g.step(6, graph=True)
+    for x, y in zip(s.get_state(0)[1], g.get_state(0)[1]):
+        assert np.array_equal(x, y)
+
+
+def test_batched_instances_equal_single_instance_runs():
+    """A batch of 8 independent N=16 chains (the batched workload's model,
+    chi_max drawn per instance) against the same instances run one by one,
+    and one instance against the oracle."""
+    wl = W.batch64_chain16(batch=8)
+    wl.chi_max[:] = [8, 16, 32, 64, 8, 16, 32, 64]
+    steps = 6
+    s = solver_for(wl, chi_cap=64)
+    s.step(steps)
+    pairs = [(0, 15), (3, 9), (7, 8)]
+    z = s.measure_1q(range(wl.n), "Z")
+    zz = s.measure_2q(pairs, "ZZ", connected=True)
+    for b in range(wl.batch):
+        w1 = wl.instance(b)
+        s1 = solver_for(w1, chi_cap=64)
+        s1.step(steps)
+        assert np.abs(s1.measure_1q(range(wl.n), "Z")[0] - z[b]).max() <= 1e-12
+        assert np.abs(s1.measure_2q(pairs, "ZZ", connected=True)[0] - zz[b]).max() <= 1e-12
+    o = oracle_run(wl, 3, steps, forced=[int(k) for k in s.rank_log(steps)[3]])
+    assert np.abs(o.z() - z[3]).max() <= TOL
