@@ -67,7 +67,11 @@ typedef struct {
     int batch;               /* B >= 1 independent instances sharing one bond graph */
     int chi_cap;             /* capacity bond dimension, >= every chi_max, <= 512 */
     int precision;           /* MPDO_FP64 | MPDO_MIXED_TF32 | MPDO_MIXED_BF16X3 */
-    int storage;             /* MPDO_STORE_F64 | MPDO_STORE_F32 */
+    int storage;             /* MPDO_STORE_F64 | MPDO_STORE_F32: element type of the stored site
+                                tensors (f32: half the memory; every contraction, the SVD
+                                and the measurements still compute in FP64 or the chosen
+                                mixed precision, and round the new sites to float).  The
+                                gradient needs MPDO_STORE_F64. */
     int trotter_order;       /* 2 (symmetric second-order product) */
     int force_trace;         /* 1: rho /= tr rho after every step (App. B b_force_rho_trace) */
     int jacobi_max_sweeps;   /* sweep limit of the Jacobi SVD (default 100, at most 128) */

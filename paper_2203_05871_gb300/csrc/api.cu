@@ -33,11 +33,11 @@ int fail(int code, const std::string& msg) {
 
 namespace {
 // rho(t0) site vectors: v[b][q][4] -> site (b, q), element [0][s][0]
-__global__ void init_product_kernel(double* sites, const double* v, int N, int cap) {
+__global__ void init_product_kernel(void* sites, int f32, const double* v, int N, int cap) {
     const int b = blockIdx.x, q = threadIdx.x;
     if (q >= N) return;
-    double* S = sites + ((size_t)b * N + q) * (size_t)cap * 4 * cap;
-    for (int s = 0; s < 4; ++s) S[(size_t)s * cap] = v[((size_t)b * N + q) * 4 + s];
+    const size_t base = ((size_t)b * N + q) * (size_t)cap * 4 * cap;
+    for (int s = 0; s < 4; ++s) site_st(sites, base + (size_t)s * cap, v[((size_t)b * N + q) * 4 + s], f32);
 }
 
 }  // namespace
@@ -193,6 +193,22 @@ int plan_jacobi(mpdo_ctx* c, const OpDesc* h, int nops, bool fp32, int* hbase, i
     return MPDO_OK;
 }
 
+std::vector<Item> layer_items(mpdo_ctx* c, int li) {
+    std::vector<int> order(c->B);
+    for (int b = 0; b < c->B; ++b) order[b] = b;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return c->chi_max[x] > c->chi_max[y]; });
+    std::vector<Item> items;
+    for (int b : order)
+        for (int i = 0; i < (int)c->layers[li].size(); ++i) items.push_back(Item{b, li, i});
+    return items;
+}
+
+int chunk_ops(mpdo_ctx* c) {
+    const auto mm = std::minmax_element(c->chi_max.begin(), c->chi_max.end());
+    if (*mm.first == *mm.second) return c->slots;
+    return std::max(1, std::min(c->slots, std::max(16, c->jacobi_resident / 4)));
+}
+
 void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     const int N = c->N, cap = c->cap, ld = c->ld;
     const size_t mat = (size_t)ld * ld;
@@ -214,8 +230,9 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.chi_max = c->chi_max[b];
     d.cutoff = c->cutoff[b];
     d.G = c->d_gates + ((size_t)b * c->n_ops + d.op) * 256;
-    d.A = site(c, b, p);
-    d.B = site(c, b, p + 1);
+    d.A = site_v(c, b, p);
+    d.B = site_v(c, b, p + 1);
+    d.site_f32 = sites_f32(c);
     d.lam_left = p > 0 ? c->d_lam + ((size_t)b * N + (p - 1)) * cap : nullptr;
     d.lam_out = c->d_lam + ((size_t)b * N + p) * cap;
     d.thetap = c->d_thetap + (size_t)s * mat;
@@ -268,8 +285,9 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         int nc = 0, max_rows = 1;
         for (int s = 0; s < nops; ++s) {
             const OpDesc& d = c->h_desc[s];
-            hc[nc++] = Copy2D{d.A, tape[s].A, 4 * d.cl, d.cm, cap, d.cm, 1.0};
-            hc[nc++] = Copy2D{d.B, tape[s].B, 4 * d.cm, d.cr, cap, d.cr, 1.0};
+            // (the gradient runs on FP64 site storage only)
+            hc[nc++] = Copy2D{static_cast<const double*>(d.A), tape[s].A, 4 * d.cl, d.cm, cap, d.cm, 1.0};
+            hc[nc++] = Copy2D{static_cast<const double*>(d.B), tape[s].B, 4 * d.cm, d.cr, cap, d.cr, 1.0};
             if (d.lam_left) hc[nc++] = Copy2D{d.lam_left, tape[s].lam, 1, d.cl, cap, d.cl, 1.0};
             max_rows = std::max(max_rows, 4 * std::max(d.cl, d.cm));
         }
@@ -450,7 +468,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
 
 int normalize_trace(mpdo_ctx* c) {
     ProfScope p_trace(c, K_TRACE);
-    CU(launch_trace_normalize(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
+    CU(launch_trace_normalize(c->d_sites, sites_f32(c), c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
                               c->d_status, c->st));
     p_trace.stop();
     prof_collect(c, K_TRACE, 0.0);
@@ -540,7 +558,8 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
     if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32 && cfg->precision != MPDO_MIXED_BF16X3)
         return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
-    if (cfg->storage != MPDO_STORE_F64) return fail(MPDO_EINVAL, "storage: only MPDO_STORE_F64 is available");
+    if (cfg->storage != MPDO_STORE_F64 && cfg->storage != MPDO_STORE_F32)
+        return fail(MPDO_EINVAL, "storage must be MPDO_STORE_F64 or MPDO_STORE_F32");
     if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
     if (cfg->jacobi_max_sweeps < 1 || cfg->jacobi_max_sweeps > kMaxSweepsCap)
         return fail(MPDO_EINVAL, "jacobi_max_sweeps must be in [1, 128]");
@@ -565,7 +584,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
         return code;
     };
     cudaError_t e;
-    if ((e = dalloc(&c->d_sites, (size_t)B * N * site_elems(c))) != cudaSuccess ||
+    if ((e = dalloc(&c->d_sites, ((size_t)B * N * site_elems(c) * site_esize(c) + 7) / 8)) != cudaSuccess ||
         (e = dalloc(&c->d_lam, (size_t)B * N * c->cap)) != cudaSuccess ||
         (e = dalloc(&c->d_dims, (size_t)B * (N + 1))) != cudaSuccess ||
         (e = dalloc(&c->d_status, (size_t)B)) != cudaSuccess ||
@@ -688,9 +707,9 @@ int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
                 v[3] += r2;
             }
         }
-    CU(cudaMemsetAsync(c->d_sites, 0, sizeof(double) * (size_t)B * N * site_elems(c), c->st));
+    CU(cudaMemsetAsync(c->d_sites, 0, site_esize(c) * (size_t)B * N * site_elems(c), c->st));
     CU(cudaMemcpyAsync(c->d_one_a, v0.data(), sizeof(double) * v0.size(), cudaMemcpyHostToDevice, c->st));
-    init_product_kernel<<<B, 64, 0, c->st>>>(c->d_sites, c->d_one_a, N, c->cap);
+    init_product_kernel<<<B, 64, 0, c->st>>>(c->d_sites, sites_f32(c), c->d_one_a, N, c->cap);
     CU(cudaGetLastError());
     std::vector<double> ones((size_t)B * N * c->cap, 1.0);
     CU(cudaMemcpyAsync(c->d_lam, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, c->st));
@@ -718,12 +737,10 @@ int mpdo_trotter_step(mpdo_ctx* c, int n_steps) {
     ++c->gen;
     for (int step = 0; step < n_steps; ++step) {
         for (int li = 0; li < (int)c->layers.size(); ++li) {
-            std::vector<Item> items;
-            for (int b = 0; b < c->B; ++b)
-                for (int i = 0; i < (int)c->layers[li].size(); ++i) items.push_back(Item{b, li, i});
-            for (size_t s0 = 0; s0 < items.size(); s0 += c->slots) {
-                std::vector<Item> chunk(items.begin() + s0,
-                                        items.begin() + std::min(items.size(), s0 + (size_t)c->slots));
+            const std::vector<Item> items = layer_items(c, li);
+            const size_t cs = (size_t)chunk_ops(c);
+            for (size_t s0 = 0; s0 < items.size(); s0 += cs) {
+                std::vector<Item> chunk(items.begin() + s0, items.begin() + std::min(items.size(), s0 + cs));
                 int rc = run_chunk(c, chunk, step, nullptr, nullptr, true);
                 if (rc) return rc;
             }
@@ -745,9 +762,10 @@ int mpdo_measure_1q(mpdo_ctx* c, const int* qubits, int nq, char comp, double* o
         if (qubits[k] < 0 || qubits[k] >= c->N) return fail(MPDO_EINVAL, "qubit index out of range");
     if (nq == 0) return MPDO_OK;
     CU(cudaMemcpyAsync(c->d_q, qubits, sizeof(int) * nq, cudaMemcpyHostToDevice, c->st));
-    CU(launch_environments(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->st));
+    CU(launch_environments(c->d_sites, sites_f32(c), c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->st));
     double* dst = out_on_device ? out : c->d_out;
-    CU(launch_measure_1q(c->d_sites, c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->d_q, nq, a, dst, c->st));
+    CU(launch_measure_1q(c->d_sites, sites_f32(c), c->d_dims, c->N, c->B, c->cap, c->d_envL, c->d_envR, c->d_q, nq,
+                         a, dst, c->st));
     if (!out_on_device) {
         CU(cudaMemcpyAsync(out, c->d_out, sizeof(double) * nq * c->B, cudaMemcpyDeviceToHost, c->st));
         CU(cudaStreamSynchronize(c->st));
@@ -769,12 +787,14 @@ int mpdo_measure_2q(mpdo_ctx* c, const int* pairs, int np, const char comp[2], i
         const int i = pairs[2 * k], j = pairs[2 * k + 1];
         if (i < 0 || j < 0 || i >= N || j >= N || i == j) return fail(MPDO_EINVAL, "pair indices out of range or i == j");
     }
-    CU(launch_environments(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->st));
+    CU(launch_environments(c->d_sites, sites_f32(c), c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->st));
     std::vector<int> allq(N);
     for (int q = 0; q < N; ++q) allq[q] = q;
     CU(cudaMemcpyAsync(c->d_q, allq.data(), sizeof(int) * N, cudaMemcpyHostToDevice, c->st));
-    CU(launch_measure_1q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, ca, c->d_one_a, c->st));
-    CU(launch_measure_1q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, cb, c->d_one_b, c->st));
+    CU(launch_measure_1q(c->d_sites, sites_f32(c), c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, ca,
+                         c->d_one_a, c->st));
+    CU(launch_measure_1q(c->d_sites, sites_f32(c), c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, c->d_q, N, cb,
+                         c->d_one_b, c->st));
     double* dst = out_on_device ? out : c->d_out;
     for (int pass = 0; pass < 2; ++pass) {
         // pass 0: pairs with i < j; pass 1: pairs with i > j, evaluated as (j, i) with swapped components
@@ -792,8 +812,8 @@ int mpdo_measure_2q(mpdo_ctx* c, const int* pairs, int np, const char comp[2], i
         if (trip.empty()) continue;
         const int x = pass == 0 ? ca : cb, y = pass == 0 ? cb : ca;
         CU(cudaMemcpyAsync(c->d_need, need.data(), N, cudaMemcpyHostToDevice, c->st));
-        CU(launch_measure_2q(c->d_sites, c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, x, y, c->d_need, c->d_full,
-                             c->st));
+        CU(launch_measure_2q(c->d_sites, sites_f32(c), c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, x, y, c->d_need,
+                             c->d_full, c->st));
         CU(cudaMemcpyAsync(c->d_pairs, trip.data(), sizeof(int) * trip.size(), cudaMemcpyHostToDevice, c->st));
         const double* oa = pass == 0 ? c->d_one_a : c->d_one_b;
         const double* ob = pass == 0 ? c->d_one_b : c->d_one_a;
@@ -831,17 +851,21 @@ int mpdo_set_state(mpdo_ctx* c, int b, const int* dims, const double* tensors) {
     if (dims[0] != 1 || dims[N] != 1) return fail(MPDO_EINVAL, "dims[0] and dims[N] must be 1");
     for (int p = 1; p < N; ++p)
         if (dims[p] < 1 || dims[p] > c->chi_max[b]) return fail(MPDO_ECAPACITY, "bond dimension out of [1, chi_max]");
+    // compact rows (l, s) of length cr, copied into rows of length chi_cap
+    const size_t es = site_esize(c);
+    std::vector<float> f32;
+    if (sites_f32(c)) {
+        size_t tot = 0;
+        for (int p = 0; p < N; ++p) tot += (size_t)dims[p] * 4 * dims[p + 1];
+        f32.assign(tensors, tensors + tot);
+    }
     size_t off = 0;
-    std::vector<double> buf((size_t)c->cap * 4 * c->cap);
     for (int p = 0; p < N; ++p) {
         const int cl = dims[p], cr = dims[p + 1];
-        std::fill(buf.begin(), buf.end(), 0.0);
-        for (int l = 0; l < cl; ++l)
-            for (int s = 0; s < 4; ++s)
-                for (int r = 0; r < cr; ++r) buf[((size_t)l * 4 + s) * c->cap + r] = tensors[off + ((size_t)l * 4 + s) * cr + r];
+        const void* src = sites_f32(c) ? (const void*)(f32.data() + off) : (const void*)(tensors + off);
+        CU(cudaMemcpy2DAsync(site_v(c, b, p), es * c->cap, src, es * cr, es * cr, (size_t)4 * cl,
+                             cudaMemcpyHostToDevice, c->st));
         off += (size_t)cl * 4 * cr;
-        CU(cudaMemcpyAsync(site(c, b, p), buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, c->st));
-        CU(cudaStreamSynchronize(c->st));
     }
     std::vector<double> ones((size_t)N * c->cap, 1.0);
     CU(cudaMemcpyAsync(c->d_lam + (size_t)b * N * c->cap, ones.data(), sizeof(double) * ones.size(),
@@ -865,17 +889,19 @@ int mpdo_get_state(mpdo_ctx* c, int b, int* dims, double* tensors, long long cap
     for (int p = 0; p < N; ++p) need += (long long)dims[p] * 4 * dims[p + 1];
     if (!tensors) return MPDO_OK;
     if (need > cap_elems) return fail(MPDO_ECAPACITY, "tensor buffer too small");
-    std::vector<double> buf((size_t)c->cap * 4 * c->cap);
+    const size_t es = site_esize(c);
+    std::vector<float> f32(sites_f32(c) ? (size_t)need : 0);
     size_t off = 0;
     for (int p = 0; p < N; ++p) {
-        CU(cudaMemcpyAsync(buf.data(), site(c, b, p), sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, c->st));
-        CU(cudaStreamSynchronize(c->st));
         const int cl = dims[p], cr = dims[p + 1];
-        for (int l = 0; l < cl; ++l)
-            for (int s = 0; s < 4; ++s)
-                for (int r = 0; r < cr; ++r) tensors[off + ((size_t)l * 4 + s) * cr + r] = buf[((size_t)l * 4 + s) * c->cap + r];
+        void* dst = sites_f32(c) ? (void*)(f32.data() + off) : (void*)(tensors + off);
+        CU(cudaMemcpy2DAsync(dst, es * cr, site_v(c, b, p), es * c->cap, es * cr, (size_t)4 * cl,
+                             cudaMemcpyDeviceToHost, c->st));
         off += (size_t)cl * 4 * cr;
     }
+    CU(cudaStreamSynchronize(c->st));
+    if (sites_f32(c))
+        for (size_t i = 0; i < f32.size(); ++i) tensors[i] = f32[i];
     return MPDO_OK;
 }
 

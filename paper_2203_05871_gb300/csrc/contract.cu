@@ -38,12 +38,12 @@ __global__ void __launch_bounds__(256) merge_gate_kernel(const OpDesc* descs, in
         for (int e = t; e < TL * 4 * KT; e += 256) {
             const int l = e / (4 * KT), s = (e / KT) & 3, kk = e % KT;
             const int gl = l0 + l, gm = m0 + kk;
-            As[l][s][kk] = (gl < d.cl && gm < d.cm) ? d.A[((size_t)gl * 4 + s) * chi_cap + gm] : 0.0;
+            As[l][s][kk] = (gl < d.cl && gm < d.cm) ? site_ld(d.A, ((size_t)gl * 4 + s) * chi_cap + gm, d.site_f32) : 0.0;
         }
         for (int e = t; e < KT * 4 * TR; e += 256) {
             const int kk = e / (4 * TR), s = (e / TR) & 3, r = e % TR;
             const int gm = m0 + kk, gr = r0 + r;
-            Bs[kk][s][r] = (gm < d.cm && gr < d.cr) ? d.B[((size_t)gm * 4 + s) * chi_cap + gr] : 0.0;
+            Bs[kk][s][r] = (gm < d.cm && gr < d.cr) ? site_ld(d.B, ((size_t)gm * 4 + s) * chi_cap + gr, d.site_f32) : 0.0;
         }
         __syncthreads();
 #pragma unroll 4
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(const OpDesc* descs, i
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int gj = j0 + tx * 4 + v;
-            if (gj < k) d.A[(size_t)gi * chi_cap + gj] = acc[u][v];
+            if (gj < k) site_st(d.A, (size_t)gi * chi_cap + gj, acc[u][v], d.site_f32);
         }
     }
 }

@@ -9,7 +9,7 @@
 namespace mpdo {
 
 // per-op sync words: [0] barrier arrivals, [1] abort flag, [8 + s] rotations in Jacobi sweep s
-constexpr int kSyncWords = 8 + kMaxSweepsCap;
+constexpr int kSyncWords = 8 + 2 * kMaxSweepsCap;   // flags, rotations per sweep, largest off-orthogonality per sweep
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

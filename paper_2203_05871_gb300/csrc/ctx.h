@@ -71,7 +71,7 @@ struct mpdo_ctx {
     std::vector<int> chi_max;
     std::vector<double> cutoff;
     // state (device)
-    double* d_sites = nullptr;    // [B][N][cap][4][cap]
+    double* d_sites = nullptr;    // [B][N][cap][4][cap], float elements when cfg.storage == MPDO_STORE_F32
     double* d_lam = nullptr;      // [B][N][cap]   lambda_p for p = 0..N-2
     int* d_dims = nullptr;        // [B][N+1]
     int* d_status = nullptr;      // [B]
@@ -132,6 +132,13 @@ namespace mpdo {
 void free_all(mpdo_ctx* c);
 int release_slots(mpdo_ctx* c);
 inline size_t site_elems(const mpdo_ctx* c) { return (size_t)c->cap * 4 * c->cap; }
+inline int sites_f32(const mpdo_ctx* c) { return c->cfg.storage == MPDO_STORE_F32 ? 1 : 0; }
+inline size_t site_esize(const mpdo_ctx* c) { return sites_f32(c) ? sizeof(float) : sizeof(double); }
+// site tensor (b, p), as stored (double or float)
+inline void* site_v(mpdo_ctx* c, int b, int p) {
+    return reinterpret_cast<char*>(c->d_sites) + ((size_t)b * c->N + p) * site_elems(c) * site_esize(c);
+}
+// site tensor (b, p) of an FP64-stored state (the adjoint requires MPDO_STORE_F64)
 inline double* site(mpdo_ctx* c, int b, int p) { return c->d_sites + ((size_t)b * c->N + p) * site_elems(c); }
 int check_status_code(mpdo_ctx* c);
 
@@ -159,6 +166,13 @@ inline int tuned_block_rows(const mpdo_ctx* c, int cl, int cr, bool fp32, int df
 // Co-resident CTA plan of the Jacobi launch over h[0..nops): hbase receives
 // [op of each CTA | rank | CTAs per op], total the number of CTAs.
 int plan_jacobi(mpdo_ctx* c, const OpDesc* h, int nops, bool fp32, int* hbase, int& total);
+
+// The (instance, op) items of layer li, instances with the larger chi_max first
+// (stable), and the number of ops per chunk: `slots`, or at most a quarter of
+// the co-resident Jacobi CTAs (>= 16) when the instances' chi_max differ, so
+// that the large ops of a chunk get their share of CTAs instead of one each.
+std::vector<Item> layer_items(mpdo_ctx* c, int li);
+int chunk_ops(mpdo_ctx* c);
 
 // Descriptor of item `it` in workspace slot s, with the bond dimensions of
 // c->h_dims (forced rank and tape cleared).

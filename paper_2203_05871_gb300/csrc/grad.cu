@@ -349,12 +349,6 @@ int run_bwd_chunk(mpdo_ctx* c, GradState* g, const std::vector<const TapeRec*>& 
     return MPDO_OK;
 }
 
-std::vector<Item> layer_items(mpdo_ctx* c, int li) {
-    std::vector<Item> items;
-    for (int b = 0; b < c->B; ++b)
-        for (int i = 0; i < (int)c->layers[li].size(); ++i) items.push_back(Item{b, li, i});
-    return items;
-}
 
 // tape layout of step s from its checkpointed dims and recorded ranks
 int plan_tape(mpdo_ctx* c, GradState* g, int s, std::vector<std::vector<TapeRec>>& recs) {
@@ -427,6 +421,7 @@ int mpdo_grad_forward(mpdo_ctx* c, int n_steps) {
     CU(cudaSetDevice(c->dev));
     if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
     if (n_steps < 1) return fail(MPDO_EINVAL, "n_steps must be >= 1");
+    if (sites_f32(c)) return fail(MPDO_EINVAL, "the gradient needs MPDO_STORE_F64 site storage");
     if (!c->grad) {
         c->grad = new (std::nothrow) GradState();
         if (!c->grad) return fail(MPDO_ENOMEM, "host allocation failed");
@@ -446,9 +441,9 @@ int mpdo_grad_forward(mpdo_ctx* c, int n_steps) {
         if (rc) return rc;
         for (int li = 0; li < (int)c->layers.size(); ++li) {
             std::vector<Item> items = layer_items(c, li);
-            for (size_t s0 = 0; s0 < items.size(); s0 += c->slots) {
-                std::vector<Item> chunk(items.begin() + s0,
-                                        items.begin() + std::min(items.size(), s0 + (size_t)c->slots));
+            const size_t cs = (size_t)chunk_ops(c);
+            for (size_t s0 = 0; s0 < items.size(); s0 += cs) {
+                std::vector<Item> chunk(items.begin() + s0, items.begin() + std::min(items.size(), s0 + cs));
                 rc = run_chunk(c, chunk, step, nullptr, nullptr, true);
                 if (rc) return rc;
             }
@@ -527,8 +522,9 @@ int mpdo_grad_backward(mpdo_ctx* c, const double* zbar, const double* wbar, doub
         // recompute the step, taping every op
         for (int li = 0; li < (int)c->layers.size(); ++li) {
             const std::vector<TapeRec>& L = recs[li];
-            for (size_t s0 = 0; s0 < L.size(); s0 += c->slots) {
-                const size_t s1 = std::min(L.size(), s0 + (size_t)c->slots);
+            const size_t cs = (size_t)chunk_ops(c);
+            for (size_t s0 = 0; s0 < L.size(); s0 += cs) {
+                const size_t s1 = std::min(L.size(), s0 + cs);
                 std::vector<Item> chunk;
                 std::vector<int> forced;
                 std::vector<TapeSlot> tape;

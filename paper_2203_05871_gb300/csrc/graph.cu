@@ -205,8 +205,8 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
             klog_kernel<<<(nops + 127) / 128, 128, 0, st>>>(ch.d_desc, nops, c->n_ops, g->d_klog);
             CU(cudaGetLastError());
         }
-    CU(launch_trace_normalize(c->d_sites, c->d_dims, c->N, c->B, cap, c->cfg.force_trace, c->d_trace, c->d_status,
-                              st));
+    CU(launch_trace_normalize(c->d_sites, sites_f32(c), c->d_dims, c->N, c->B, cap, c->cfg.force_trace, c->d_trace,
+                              c->d_status, st));
     return MPDO_OK;
 }
 
@@ -220,11 +220,10 @@ int build_graph(mpdo_ctx* c, GraphState* g) {
     CU(cudaMemsetAsync(g->d_error, 0, sizeof(int), c->st));
     g->chunks.assign(c->layers.size(), {});
     for (int li = 0; li < (int)c->layers.size(); ++li) {
-        std::vector<Item> items;
-        for (int b = 0; b < c->B; ++b)
-            for (int i = 0; i < (int)c->layers[li].size(); ++i) items.push_back(Item{b, li, i});
-        for (size_t s0 = 0; s0 < items.size(); s0 += c->slots) {
-            const int nops = (int)std::min((size_t)c->slots, items.size() - s0);
+        const std::vector<Item> items = layer_items(c, li);
+        const size_t cs = (size_t)chunk_ops(c);
+        for (size_t s0 = 0; s0 < items.size(); s0 += cs) {
+            const int nops = (int)std::min(cs, items.size() - s0);
             if (nops > kMaxChunk || nops > std::min(g->Rj, g->Rq))
                 return fail(MPDO_ECAPACITY, "graph step: more ops in one chunk than co-resident CTAs");
             Chunk ch;

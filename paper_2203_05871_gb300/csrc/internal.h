@@ -49,8 +49,9 @@ struct OpDesc {
     int chi_max;
     double cutoff;
     const double* G;   // 16x16 gate, row-major G[(s1' s2'), (s1 s2)]
-    double* A;         // site p    [cl][4][chi_cap]
-    double* B;         // site p+1  [cm][4][chi_cap]
+    void* A;           // site p    [cl][4][chi_cap] (double, or float when site_f32)
+    void* B;           // site p+1  [cm][4][chi_cap]
+    int site_f32;      // site tensors stored as float (MPDO_STORE_F32)
     const double* lam_left;  // lambda_{p-1} (nullptr => 1)
     double* lam_out;   // lambda_p
     double* thetap;    // Theta'  m x n (ld)
@@ -74,6 +75,17 @@ struct OpDesc {
     double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr
     double* tape_s;    // adjoint recompute: all c sorted singular values
 };
+
+// Site tensor element i as double (storage f64 or f32), and the store back.
+__device__ __forceinline__ double site_ld(const void* p, size_t i, int f32) {
+    return f32 ? (double)static_cast<const float*>(p)[i] : static_cast<const double*>(p)[i];
+}
+__device__ __forceinline__ void site_st(void* p, size_t i, double v, int f32) {
+    if (f32)
+        static_cast<float*>(p)[i] = (float)v;
+    else
+        static_cast<double*>(p)[i] = v;
+}
 
 // ---------------------------------------------------------------------------
 // kernel launchers (each returns the cudaError_t of the launch)
@@ -155,17 +167,17 @@ struct GemmDesc {
 cudaError_t launch_gemm(const GemmDesc* d_desc, int count, int max_m, int max_n, bool fp32_compute,
                         cudaStream_t st);
 
-cudaError_t launch_trace_normalize(double* sites, const int* dims, int n, int B, int chi_cap,
+cudaError_t launch_trace_normalize(void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                                    int force, double* trace_out, int* status, cudaStream_t st);
-cudaError_t launch_environments(const double* sites, const int* dims, int n, int B, int chi_cap,
+cudaError_t launch_environments(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                                 double* envL, double* envR, cudaStream_t st);
 // E(comp at q) for the listed qubits: out[b][k] = <sigma^c_q> (divided by E0)
-cudaError_t launch_measure_1q(const double* sites, const int* dims, int n, int B, int chi_cap,
+cudaError_t launch_measure_1q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                               const double* envL, const double* envR, const int* d_q, int nq,
                               int comp, double* out, cudaStream_t st);
 // all-pairs propagation: for each (b, i) computes E(ca at i, cb at j) for j > i
 // into full[b][i][j]; unused entries untouched.
-cudaError_t launch_measure_2q(const double* sites, const int* dims, int n, int B, int chi_cap,
+cudaError_t launch_measure_2q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                               const double* envL, const double* envR, int ca, int cb,
                               const unsigned char* d_need_i, double* full, cudaStream_t st);
 // d_trip[m][3] = (i, j, k): out[b][k] = full[b][i][j] (- one_a[b][i] one_b[b][j] if connected)

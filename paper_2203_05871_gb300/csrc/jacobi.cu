@@ -78,6 +78,7 @@ struct Ctx {
     T* rows;          // [2b][rowlen] in shared memory
     T* nrm;           // [2b]
     int* rid;         // [2b] global row index or -1
+    unsigned* rho2;   // largest g^2 / (a b) rotated in this CTA and sweep (float bits)
     int rowlen, L;    // row length in smem (W part + Z part), W part length
     T floor2, tol;
 };
@@ -150,6 +151,7 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     T cs, sn, t;
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
+    if (lane == 0) atomicMax(C.rho2, __float_as_uint((float)(g / a * (g / b))));
     int i = lane;
     for (; i + 96 < C.rowlen; i += 128) {
         T x[4], y[4];
@@ -181,6 +183,97 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     return 1;
 }
 
+// Cross pairs of the FP32 pass with one block-0 row per warp (b <= JW): warp
+// w keeps row w in registers while the b rows of block 1 pass by, so each
+// rotation reads and writes only the partner row in shared memory (the pass
+// is bound by shared-memory bandwidth, not by FP32 arithmetic).
+constexpr int kRegU = 64;   // row elements per lane held in registers (rows <= 2048)
+
+__device__ int cross_pairs_in_registers(const Ctx<float>& C, int b, int warp, int lane) {
+    float x[kRegU];
+    const bool own = warp < b && C.rid[warp] >= 0;
+    float a = 0.0f;
+    if (own) {
+        const float* rp = C.rows + (size_t)warp * C.rowlen;
+#pragma unroll
+        for (int u = 0; u < kRegU; ++u) {
+            const int e = u * 32 + lane;
+            x[u] = e < C.rowlen ? rp[e] : 0.0f;
+        }
+        a = C.nrm[warp];
+    }
+    int rot = 0;
+    for (int t = 0; t < b; ++t) {
+        const int q = b + (warp + t) % b;
+        if (own && C.rid[q] >= 0) {
+            float* rq = C.rows + (size_t)q * C.rowlen;
+            const float bq = C.nrm[q];
+            if (a <= C.floor2 || bq <= C.floor2) {
+                if (a <= C.floor2 && a != 0.0f) {
+#pragma unroll
+                    for (int u = 0; u < kRegU; ++u) x[u] = 0.0f;
+                    a = 0.0f;
+                }
+                if (bq <= C.floor2 && bq != 0.0f) {
+                    for (int i = lane; i < C.L; i += 32) rq[i] = 0.0f;
+                    __syncwarp();
+                    if (lane == 0) C.nrm[q] = 0.0f;
+                }
+            } else {
+                float g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+                for (int u = 0; u < kRegU; u += 2) {
+                    const int e0 = u * 32 + lane, e1 = e0 + 32;
+                    if (e0 < C.L) g0 = fmaf(x[u], rq[e0], g0);
+                    if (e1 < C.L) g1 = fmaf(x[u + 1], rq[e1], g1);
+                }
+                const float g = warp_sum(g0 + g1);
+                if (g != 0.0f && fabsf(g) > C.tol * sqrtf(a) * sqrtf(bq)) {
+                    float cs, sn, tt;
+                    rot_params(a, bq, g, cs, sn, tt);
+                    if (tt != 0.0f) {
+#pragma unroll
+                        for (int u = 0; u < kRegU; ++u) {
+                            const int e = u * 32 + lane;
+                            if (e < C.rowlen) {
+                                const float y = rq[e];
+                                rq[e] = fmaf(sn, x[u], cs * y);
+                                x[u] = fmaf(cs, x[u], -sn * y);
+                            }
+                        }
+                        __syncwarp();
+                        float na = fmaf(-tt, g, a), nb = fmaf(tt, g, bq);
+                        if (na < 0.1f * a) {
+                            float s0 = 0.0f;
+#pragma unroll
+                            for (int u = 0; u < kRegU; ++u)
+                                if (u * 32 + lane < C.L) s0 = fmaf(x[u], x[u], s0);
+                            na = warp_sum(s0);
+                        }
+                        if (nb < 0.1f * bq) nb = row_dot(rq, rq, C.L, lane);
+                        a = na;
+                        if (lane == 0) C.nrm[q] = nb;
+                        ++rot;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (own) {
+        float* rp = C.rows + (size_t)warp * C.rowlen;
+#pragma unroll
+        for (int u = 0; u < kRegU; ++u) {
+            const int e = u * 32 + lane;
+            if (e < C.rowlen) rp[e] = x[u];
+        }
+        __syncwarp();
+        if (lane == 0) C.nrm[warp] = a;
+    }
+    __syncthreads();
+    return rot;
+}
+
 // All pairs inside each of the two blocks (circle method, first round of a
 // sweep only), then all cross pairs between the two blocks.
 template <typename T>
@@ -198,6 +291,9 @@ __device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, 
             }
             __syncthreads();
         }
+    }
+    if constexpr (sizeof(T) == 4) {
+        if (b <= JW && C.rowlen <= 32 * kRegU) return rot + cross_pairs_in_registers(C, b, warp, lane);
     }
     for (int t = 0; t < b; ++t) {
         for (int i = warp; i < b; i += JW) rot += pair_rotate(C, i, b + (i + t) % b, lane);
@@ -234,6 +330,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     unsigned gen = 0;
     __shared__ double s_floor2, s_scale;
     __shared__ int s_conv;
+    __shared__ unsigned s_rho2;
 
     Ctx<T> C;
     C.rowlen = L + zl;
@@ -241,6 +338,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     C.rows = reinterpret_cast<T*>(smem_raw);
     C.nrm = C.rows + (size_t)2 * b * C.rowlen;
     C.rid = reinterpret_cast<int*>(C.nrm + 2 * b);
+    C.rho2 = &s_rho2;
     {
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
         const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
@@ -299,6 +397,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         int used = 0;
         for (int sweep = 0; sweep < sweeps && !conv; ++sweep) {
             int rot = 0;
+            if (threadIdx.x == 0) s_rho2 = 0u;
             // fresh squared row norms, then the tail threshold (same in every CTA)
             for (int row = g * JW + warp; row < c; row += G * JW) {
                 const T* w = W + (size_t)row * ld;
@@ -352,12 +451,21 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                     }
                     __syncthreads();
                 }
-                if (r == nbp - 2 && lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
+                if (r == nbp - 2) {
+                    if (lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
+                    __syncthreads();
+                    if (threadIdx.x == 0 && s_rho2) atomicMax(&sw[8 + kMaxSweepsCap + sweep], s_rho2);
+                }
                 if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             }
             // FP32 pass: done when fewer than c/4 pairs still rotate (a few pairs
             // sit at FP32's resolution forever; the FP64 pass finishes them)
-            if (threadIdx.x == 0) s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u));
+            // FP64: also converged when the largest relative off-orthogonality rotated
+            // away was below 1e-10: the next sweep would meet pairs at ~1e-20, far
+            // under tol, and rotate nothing
+            if (threadIdx.x == 0)
+                s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u)) ||
+                         (!kF32 && __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= 1e-20f);
             __syncthreads();
             conv = s_conv;
             used = sweep + 1;

@@ -17,15 +17,22 @@ namespace {
 
 constexpr int MT = 512;
 
-__device__ __forceinline__ const double* site_ptr(const double* sites, int b, int p, int n, int cap) {
-    return sites + ((size_t)b * n + p) * (size_t)cap * 4 * cap;
-}
-__device__ __forceinline__ double* site_ptr(double* sites, int b, int p, int n, int cap) {
-    return sites + ((size_t)b * n + p) * (size_t)cap * 4 * cap;
+// one site tensor, read as double whatever the storage (f64 or f32)
+struct SiteRef {
+    const void* p;
+    int f32;
+    __device__ double operator[](size_t i) const { return site_ld(p, i, f32); }
+};
+
+__device__ __forceinline__ SiteRef site_ptr(const void* sites, int f32, int b, int p, int n, int cap) {
+    const size_t off = ((size_t)b * n + p) * (size_t)cap * 4 * cap;
+    return SiteRef{f32 ? (const void*)(static_cast<const float*>(sites) + off)
+                       : (const void*)(static_cast<const double*>(sites) + off),
+                   f32};
 }
 
 // v_out[r] = sum_l v_in[l] S[l][a][r]   (row vector times one Pauli slice)
-__device__ void vec_slice(const double* S, int a, int cl, int cr, int cap, const double* vin, double* vout) {
+__device__ void vec_slice(SiteRef S, int a, int cl, int cr, int cap, const double* vin, double* vout) {
     for (int r = threadIdx.x; r < cr; r += blockDim.x) {
         double acc = 0.0;
         for (int l = 0; l < cl; ++l) acc = fma(vin[l], S[((size_t)l * 4 + a) * cap + r], acc);
@@ -33,7 +40,7 @@ __device__ void vec_slice(const double* S, int a, int cl, int cr, int cap, const
     }
 }
 
-__global__ void __launch_bounds__(MT) trace_kernel(double* sites, const int* dims, int n, int cap, int force,
+__global__ void __launch_bounds__(MT) trace_kernel(void* sites, int f32, const int* dims, int n, int cap, int force,
                                                    double* trace_out, int* status) {
     const int b = blockIdx.x;
     const int* dm = dims + (size_t)b * (n + 1);
@@ -43,7 +50,7 @@ __global__ void __launch_bounds__(MT) trace_kernel(double* sites, const int* dim
     double* vin = v0;
     double* vout = v1;
     for (int p = 0; p < n; ++p) {
-        vec_slice(site_ptr(sites, b, p, n, cap), 0, dm[p], dm[p + 1], cap, vin, vout);
+        vec_slice(site_ptr(sites, f32, b, p, n, cap), 0, dm[p], dm[p + 1], cap, vin, vout);
         __syncthreads();
         double* t = vin;
         vin = vout;
@@ -58,15 +65,18 @@ __global__ void __launch_bounds__(MT) trace_kernel(double* sites, const int* dim
     }
     __syncthreads();
     if (force && isfinite(s_tr) && s_tr != 0.0) {
-        double* S = site_ptr(sites, b, 0, n, cap);
+        void* S = const_cast<void*>(site_ptr(sites, f32, b, 0, n, cap).p);
         const double inv = 1.0 / s_tr;
         const int cr = dm[1];
-        for (int e = threadIdx.x; e < 4 * cr; e += blockDim.x) S[(size_t)(e / cr) * cap + (e % cr)] *= inv;
+        for (int e = threadIdx.x; e < 4 * cr; e += blockDim.x) {
+            const size_t i = (size_t)(e / cr) * cap + (e % cr);
+            site_st(S, i, site_ld(S, i, f32) * inv, f32);
+        }
     }
 }
 
 // blockIdx.y == 0: left environments, 1: right environments
-__global__ void __launch_bounds__(MT) env_kernel(const double* sites, const int* dims, int n, int cap,
+__global__ void __launch_bounds__(MT) env_kernel(const void* sites, int f32, const int* dims, int n, int cap,
                                                  double* envL, double* envR) {
     const int b = blockIdx.x;
     const int* dm = dims + (size_t)b * (n + 1);
@@ -75,7 +85,7 @@ __global__ void __launch_bounds__(MT) env_kernel(const double* sites, const int*
         if (threadIdx.x == 0) E[0] = 1.0;
         __syncthreads();
         for (int p = 0; p < n; ++p) {
-            vec_slice(site_ptr(sites, b, p, n, cap), 0, dm[p], dm[p + 1], cap, E + (size_t)p * cap,
+            vec_slice(site_ptr(sites, f32, b, p, n, cap), 0, dm[p], dm[p + 1], cap, E + (size_t)p * cap,
                       E + (size_t)(p + 1) * cap);
             __syncthreads();
         }
@@ -85,7 +95,7 @@ __global__ void __launch_bounds__(MT) env_kernel(const double* sites, const int*
         __syncthreads();
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
         for (int p = n - 1; p >= 0; --p) {
-            const double* S = site_ptr(sites, b, p, n, cap);
+            const SiteRef S = site_ptr(sites, f32, b, p, n, cap);
             const double* rin = E + (size_t)(p + 1) * cap;
             double* rout = E + (size_t)p * cap;
             const int cl = dm[p], cr = dm[p + 1];
@@ -116,7 +126,7 @@ __device__ double block_sum(double v) {
 }
 
 // out[b*nq + k] = E(comp at q_k) / E0
-__global__ void __launch_bounds__(MT) one_kernel(const double* sites, const int* dims, int n, int cap,
+__global__ void __launch_bounds__(MT) one_kernel(const void* sites, int f32, const int* dims, int n, int cap,
                                                  const double* envL, const double* envR, const int* qs, int nq,
                                                  int comp, double* out) {
     const int k = blockIdx.x, b = blockIdx.y;
@@ -125,7 +135,7 @@ __global__ void __launch_bounds__(MT) one_kernel(const double* sites, const int*
     const double* Lq = envL + ((size_t)b * (n + 1) + q) * cap;
     const double* Rq = envR + ((size_t)b * (n + 1) + q + 1) * cap;
     const double E0 = envL[((size_t)b * (n + 1) + n) * cap];
-    const double* S = site_ptr(sites, b, q, n, cap);
+    const SiteRef S = site_ptr(sites, f32, b, q, n, cap);
     const int cl = dm[q], cr = dm[q + 1];
     double part = 0.0;
     for (int r = threadIdx.x; r < cr; r += blockDim.x) {
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(MT) one_kernel(const double* sites, const int*
 
 // for each (b, i) with need[i]: w = L_i B_i[ca]; for j > i:
 // full[b][i][j] = (w B_j[cb]) . R_{j+1} / E0 ;  w <- w B_j[I]
-__global__ void __launch_bounds__(MT) two_kernel(const double* sites, const int* dims, int n, int cap,
+__global__ void __launch_bounds__(MT) two_kernel(const void* sites, int f32, const int* dims, int n, int cap,
                                                  const double* envL, const double* envR, int ca, int cb,
                                                  const unsigned char* need, double* full) {
     const int i = blockIdx.x, b = blockIdx.y;
@@ -148,12 +158,12 @@ __global__ void __launch_bounds__(MT) two_kernel(const double* sites, const int*
     const double E0 = envL[((size_t)b * (n + 1) + n) * cap];
     __shared__ double w0[kMaxChi], w1[kMaxChi];
     const double* Li = envL + ((size_t)b * (n + 1) + i) * cap;
-    vec_slice(site_ptr(sites, b, i, n, cap), ca, dm[i], dm[i + 1], cap, Li, w0);
+    vec_slice(site_ptr(sites, f32, b, i, n, cap), ca, dm[i], dm[i + 1], cap, Li, w0);
     __syncthreads();
     double* w = w0;
     double* wn = w1;
     for (int j = i + 1; j < n; ++j) {
-        const double* S = site_ptr(sites, b, j, n, cap);
+        const SiteRef S = site_ptr(sites, f32, b, j, n, cap);
         const double* Rj = envR + ((size_t)b * (n + 1) + j + 1) * cap;
         const int cl = dm[j], cr = dm[j + 1];
         double part = 0.0;
@@ -190,29 +200,30 @@ __global__ void gather_kernel(const double* full, const double* one_a, const dou
 
 }  // namespace
 
-cudaError_t launch_trace_normalize(double* sites, const int* dims, int n, int B, int chi_cap, int force,
+cudaError_t launch_trace_normalize(void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap, int force,
                                    double* trace_out, int* status, cudaStream_t st) {
-    trace_kernel<<<B, MT, 0, st>>>(sites, dims, n, chi_cap, force, trace_out, status);
+    trace_kernel<<<B, MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, force, trace_out, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_environments(const double* sites, const int* dims, int n, int B, int chi_cap, double* envL,
-                                double* envR, cudaStream_t st) {
-    env_kernel<<<dim3(B, 2), MT, 0, st>>>(sites, dims, n, chi_cap, envL, envR);
+cudaError_t launch_environments(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
+                                double* envL, double* envR, cudaStream_t st) {
+    env_kernel<<<dim3(B, 2), MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR);
     return cudaGetLastError();
 }
 
-cudaError_t launch_measure_1q(const double* sites, const int* dims, int n, int B, int chi_cap, const double* envL,
-                              const double* envR, const int* d_q, int nq, int comp, double* out, cudaStream_t st) {
-    if (nq <= 0) return cudaSuccess;
-    one_kernel<<<dim3(nq, B), MT, 0, st>>>(sites, dims, n, chi_cap, envL, envR, d_q, nq, comp, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_measure_2q(const double* sites, const int* dims, int n, int B, int chi_cap, const double* envL,
-                              const double* envR, int ca, int cb, const unsigned char* d_need_i, double* full,
+cudaError_t launch_measure_1q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
+                              const double* envL, const double* envR, const int* d_q, int nq, int comp, double* out,
                               cudaStream_t st) {
-    two_kernel<<<dim3(n, B), MT, 0, st>>>(sites, dims, n, chi_cap, envL, envR, ca, cb, d_need_i, full);
+    if (nq <= 0) return cudaSuccess;
+    one_kernel<<<dim3(nq, B), MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR, d_q, nq, comp, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure_2q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
+                              const double* envL, const double* envR, int ca, int cb, const unsigned char* d_need_i,
+                              double* full, cudaStream_t st) {
+    two_kernel<<<dim3(n, B), MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR, ca, cb, d_need_i, full);
     return cudaGetLastError();
 }
 

@@ -82,8 +82,9 @@ extern "C" int mpdo_measure_1q_noalloc(const double* sites, const int* dims, int
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     double* envL = scratch;
     double* envR = scratch + (size_t)batch * (n_qubits + 1) * chi_cap;
-    cudaError_t e = launch_environments(sites, dims, n_qubits, batch, chi_cap, envL, envR, st);
-    if (e == cudaSuccess) e = launch_measure_1q(sites, dims, n_qubits, batch, chi_cap, envL, envR, qubits, nq, a, out, st);
+    cudaError_t e = launch_environments(sites, 0, dims, n_qubits, batch, chi_cap, envL, envR, st);
+    if (e == cudaSuccess)
+        e = launch_measure_1q(sites, 0, dims, n_qubits, batch, chi_cap, envL, envR, qubits, nq, a, out, st);
     if (e != cudaSuccess) return fail(MPDO_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
     return MPDO_OK;
 }

@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(128, 1) tc_kernel(const OpDesc* descs, int chi
             const int row = e / TK, k = e % TK;
             const int gi = i0 + row, gk = k0 + k;
             double x = 0.0;
-            if (gi < M && gk < K) x = kMerge ? d.A[(size_t)gi * chi_cap + gk] : d.thetap[(size_t)gi * ld + gk];
+            if (gi < M && gk < K) x = kMerge ? site_ld(d.A, (size_t)gi * chi_cap + gk, d.site_f32) : d.thetap[(size_t)gi * ld + gk];
             split_store(Ahi, Alo, kmajor_offset(row, k), x);
         }
         for (int e = tid; e < TN * TK; e += 128) {
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(128, 1) tc_kernel(const OpDesc* descs, int chi
                 k = e / TN;
                 col = e % TN;
                 const int s2 = col >> 4, rl = col & 15, gm = k0 + k, gr = r0 + rl;
-                if (gm < K && gr < ncols) x = d.B[((size_t)gm * 4 + s2) * chi_cap + gr];
+                if (gm < K && gr < ncols) x = site_ld(d.B, ((size_t)gm * 4 + s2) * chi_cap + gr, d.site_f32);
             } else {
                 col = e / TK;
                 k = e % TK;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(128, 1) tc_kernel(const OpDesc* descs, int chi
         if (row < M)
             for (int n = 0; n < TN; ++n) {
                 const int j = j0 + n;
-                if (j < ncols) d.A[(size_t)row * chi_cap + j] = acc[n];
+                if (j < ncols) site_st(d.A, (size_t)row * chi_cap + j, acc[n], d.site_f32);
             }
     }
 }

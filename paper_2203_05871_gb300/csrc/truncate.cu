@@ -128,13 +128,13 @@ __global__ void __launch_bounds__(TT) truncate_kernel(const OpDesc* descs, int c
     for (int j = warp; j < k; j += TT / 32) {
         const int src = perm[j];
         double* y = d.Yk + (size_t)j * ld;
-        double* bnew = d.B + (size_t)j * 4 * chi_cap;
+        const size_t bnew = (size_t)j * 4 * chi_cap;   // row j of the new site p+1
         if (d.transposed) {
             const double* zr = d.Z + (size_t)src * ld;
             for (int i = lane; i < n; i += 32) {
                 const double v = zr[i];
                 y[i] = v;
-                bnew[(i / cr) * chi_cap + (i % cr)] = v;
+                site_st(d.B, bnew + (i / cr) * chi_cap + (i % cr), v, d.site_f32);
             }
         } else {
             const double* wr = d.W + (size_t)src * ld;
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(TT) truncate_kernel(const OpDesc* descs, int c
             for (int i = lane; i < n; i += 32) {
                 const double v = wr[i] * inv;
                 y[i] = v;
-                bnew[(i / cr) * chi_cap + (i % cr)] = v;
+                site_st(d.B, bnew + (i / cr) * chi_cap + (i % cr), v, d.site_f32);
             }
         }
     }

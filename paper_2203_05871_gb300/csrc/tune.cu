@@ -8,7 +8,7 @@
 // rows and how many ops share the GPU, so it is measured: for every class the
 // tuner fills as many workspace slots as a layer has ops in flight with a
 // seeded graded matrix of the class's shape (rows scaled like the rows of a
-// pivoted R), and times the Jacobi launch for every b that fits (FP64 pass,
+// pivoted R; at most 16 slots), and times the Jacobi launch for every b that fits (FP64 pass,
 // and the FP32 pass of the mixed path), keeping the fastest.  The winners go
 // to a (chi_l, chi_r) table that both the host-planned and the graph step
 // read.  Different b change the order of the rotations, so results change at
@@ -81,7 +81,9 @@ extern "C" int mpdo_autotune(mpdo_ctx* c, const int* classes, int n_classes, int
         if (classes[2 * i] < 1 || classes[2 * i] > cap || classes[2 * i + 1] < 1 || classes[2 * i + 1] > cap)
             return fail(MPDO_EINVAL, "class chi values must be in [1, chi_cap]");
     if (c->jb_table.empty()) c->jb_table.assign((size_t)(cap + 1) * (cap + 1) * 2, 0);
-    const int nops = std::max(1, std::min(c->slots, c->B * c->max_layer));
+    // ops in flight while timing: a layer's worth, at most 16 (enough to share
+    // the GPU the way a layer does, and keeps tuning to seconds)
+    const int nops = std::max(1, std::min(std::min(c->slots, c->B * c->max_layer), 16));
     std::mt19937_64 rng(2203058712ull);
     std::normal_distribution<double> nd(0.0, 1.0);
     int* d_status = nullptr;

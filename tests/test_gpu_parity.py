@@ -371,3 +371,42 @@ def test_batched_instances_equal_single_instance_runs():
         assert np.abs(s1.measure_2q(pairs, "ZZ", connected=True)[0] - zz[b]).max() <= 1e-12
     o = oracle_run(wl, 3, steps, forced=[int(k) for k in s.rank_log(steps)[3]])
     assert np.abs(o.z() - z[3]).max() <= TOL
+
+
+# ---------------------------------------------------------------------------
+# f32 site storage (the "complex64 storage" variant of the real Pauli basis)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_f32_storage_against_oracle(precision):
+    """Sites stored as float: observables within the mixed tolerance of the
+    FP64 oracle (each op rounds the new sites to float, ~6e-8 relative), and
+    measurably different from FP64 storage (the float rounding is real)."""
+    from paper_2203_05871_gb300 import FP64, MIXED_TF32, STORE_F32
+    prec = FP64 if precision == "fp64" else MIXED_TF32
+    wl = W.chain8_fp64()
+    s32 = solver_for(wl, precision=prec, storage=STORE_F32)
+    worst = compare_to_oracle(wl, wl.steps, s32, tol=TOL_MIXED)
+    assert worst <= TOL_MIXED
+    s64 = solver_for(wl, precision=prec)
+    s64.step(wl.steps)
+    d = np.abs(s64.measure_1q(range(wl.n), "Z") - s32.measure_1q(range(wl.n), "Z")).max()
+    assert 0.0 < d < TOL_MIXED
+
+
+def test_f32_storage_state_roundtrip_and_graph():
+    from paper_2203_05871_gb300 import STORE_F32
+    wl = W.random_model(6, W.ring_bonds(6), 72, chi_max=16, cutoff=1e-11)
+    dims, tens = W.random_mpo_state(6, 16, seed=5)
+    s = solver_for(wl, storage=STORE_F32)
+    s.set_state(0, dims, tens)
+    d2, t2 = s.get_state(0)
+    assert d2 == list(dims)
+    for x, y in zip(tens, t2):
+        assert np.array_equal(np.asarray(x, np.float32).astype(np.float64), y)
+    g = solver_for(wl, storage=STORE_F32)
+    s.set_state(0, dims, tens)
+    g.set_state(0, dims, tens)
+    s.step(3)
+    g.step(3, graph=True)
+    for x, y in zip(s.get_state(0)[1], g.get_state(0)[1]):
+        assert np.array_equal(x, y)
