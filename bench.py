@@ -318,6 +318,29 @@ def run_arm(args, precision, world, dist, local):
             "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
 
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def contraction_roofline(prof):
+    """tcgen05 merge + gate and reconstruct kernels against the TF32 tensor peak
+    (measured BF16 burst x the nominal TF32 / BF16 ratio 1.1 / 2.25)."""
+    fl = prof["merge_gate"]["flops"] + prof["reconstruct"]["flops"]
+    ms = prof["merge_gate"]["ms"] + prof["reconstruct"]["ms"]
+    bf16 = measured_peaks().get("bf16_tflops")
+    peak = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
+    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    return {"kernel": "tcgen05 merge+gate and reconstruct (TF32, 3-way operand split)", "bound": "tensor",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "note": "useful flops (each is 3 TF32 products of the split operands); peak = measured bf16 burst "
+                    "x 1.1/2.25 (nominal TF32/BF16)" + ("" if bf16 else "; of fallback")}
+
+
 def run_adjoint(args, local):
     """One gradient (checkpointed forward + backward) of sum_i zbar_i <z_i> +
     sum_{i<j} wbar_ij conn_ij on the N=24 ring (closing bond routed by swaps)
@@ -430,6 +453,7 @@ def main():
                      "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
                              "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
                              "MEASURED_PEAKS.json)"},
+        "roofline_contraction": contraction_roofline(prof) if hp == "mixed" else None,
         "autotune": {"jacobi_rows_per_block": head["tuned"],
                      "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},
         "graph_step": {"ms_per_step": head["graph_ms"] / args.steps,
