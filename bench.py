@@ -446,6 +446,8 @@ def main():
                     for k, v in prof.items() if v["launches"]},
         "jacobi_mean_sweeps": (jac["sweeps"] / jac["svds"] if jac["svds"] else None),
         "jacobi_mean_sweeps_fp32": (jac["sweeps_fp32"] / jac["svds"] if jac["svds"] else None),
+        "jacobi_critical_sweeps": ([jac["critical_sweeps"] / jac["chunks"], jac["critical_sweeps_fp32"] / jac["chunks"]]
+                                   if jac.get("chunks") else None),
         "roofline": {"kernel": "truncation SVD (jacobi_svd%s)" % (" + jacobi_fp32 + precond_gemm" if hp == "mixed"
                                                                     else ""),
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",

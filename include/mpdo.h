@@ -209,6 +209,13 @@ int mpdo_profile_read(mpdo_ctx *ctx, double *ms, long long *launches, double *fl
  * only).  Profiling must be enabled. */
 int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds, long long *sweeps_fp32);
 
+/* The critical path of the same SVDs: every chunk of ops shares one Jacobi
+ * launch per pass, which lasts as long as its slowest op.  crit and crit_fp32
+ * are the sums over chunks of the largest FP64 and FP32 sweep counts of any op
+ * in the chunk; chunks is the number of chunks.  Any pointer may be NULL.
+ * Profiling must be enabled; mpdo_profile_read(reset = 1) zeroes them. */
+int mpdo_profile_sweeps_critical(mpdo_ctx *ctx, long long *crit, long long *crit_fp32, long long *chunks);
+
 /* mpdo_measure_1q without any device allocation, on a state held in the
  * caller's device memory.  For callers that cannot call cudaMalloc: code that
  * runs while a stream is being captured into a CUDA graph, or frameworks that

@@ -150,6 +150,7 @@ int check_status_code(mpdo_ctx* c) {
     CU(cudaStreamSynchronize(c->st));
     int any = 0;
     for (int v : st) any |= v;
+    if (any & MPDO_ST_CAPACITY) return fail(MPDO_ECAPACITY, "a Jacobi block size did not fit its kernel");
     if (any & MPDO_ST_TIMEOUT) return fail(MPDO_ETIMEOUT, "a device-side wait timed out");
     if (any & MPDO_ST_NONFINITE) return fail(MPDO_ENONFINITE, "non-finite values in some instance");
     if (any & MPDO_ST_NOCONV) return fail(MPDO_ENOCONV, "Jacobi SVD hit its sweep limit in some instance");
@@ -246,7 +247,7 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.max_disc = c->d_maxdisc + b;
     d.rank_log = nullptr;
     d.jb = tuned_block_rows(c, d.cl, d.cr, false, jacobi_block_rows(d.L, d.c, 8));
-    d.jb32 = tuned_block_rows(c, d.cl, d.cr, true, jacobi_block_rows(d.L + d.c, d.c, 4));
+    d.jb32 = tuned_block_rows(c, d.cl, d.cr, true, jacobi_block_rows_f32(d.L, d.c));
     d.sweeps_out = c->d_sweeps + s;
     d.forced_k = 0;
     d.tape_V = nullptr;
@@ -436,12 +437,19 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
                        c->st));
     if (c->prof) CU(cudaMemcpyAsync(c->h_sweeps.data(), c->d_sweeps, sizeof(int) * nops, cudaMemcpyDeviceToHost, c->st));
     CU(cudaStreamSynchronize(c->st));
-    if (c->prof)
+    if (c->prof) {
+        int crit = 0, crit32 = 0;
         for (int s = 0; s < nops; ++s) {
             c->prof_sweeps += c->h_sweeps[s] & 0xffff;
             c->prof_sweeps32 += c->h_sweeps[s] >> 16;
             c->prof_svds += 1;
+            crit = std::max(crit, c->h_sweeps[s] & 0xffff);
+            crit32 = std::max(crit32, c->h_sweeps[s] >> 16);
         }
+        c->prof_crit += crit;
+        c->prof_crit32 += crit32;
+        c->prof_chunks += 1;
+    }
     double fl_rec = 0.0;
     for (int s = 0; s < nops; ++s) {
         const OpDesc& d = c->h_desc[s];
@@ -1001,6 +1009,7 @@ int mpdo_profile_read(mpdo_ctx* c, double* ms, long long* launches, double* flop
             c->prof_flops[k] = 0.0;
         }
         c->prof_sweeps = c->prof_svds = c->prof_sweeps32 = 0;
+        c->prof_crit = c->prof_crit32 = c->prof_chunks = 0;
     }
     return MPDO_OK;
 }
@@ -1010,6 +1019,14 @@ int mpdo_profile_sweeps(mpdo_ctx* c, long long* sweeps, long long* svds, long lo
     if (sweeps) *sweeps = c->prof_sweeps;
     if (svds) *svds = c->prof_svds;
     if (sweeps_fp32) *sweeps_fp32 = c->prof_sweeps32;
+    return MPDO_OK;
+}
+
+int mpdo_profile_sweeps_critical(mpdo_ctx* c, long long* crit, long long* crit_fp32, long long* chunks) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    if (crit) *crit = c->prof_crit;
+    if (crit_fp32) *crit_fp32 = c->prof_crit32;
+    if (chunks) *chunks = c->prof_chunks;
     return MPDO_OK;
 }
 

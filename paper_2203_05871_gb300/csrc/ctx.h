@@ -93,6 +93,7 @@ struct mpdo_ctx {
     mpdo::Copy2D* h_copy = nullptr;     // pinned
     std::vector<int> h_sweeps;
     long long prof_sweeps = 0, prof_svds = 0, prof_sweeps32 = 0;
+    long long prof_crit = 0, prof_crit32 = 0, prof_chunks = 0;   // per chunk: largest sweeps of any op
     mpdo::OpDesc* d_desc = nullptr;
     mpdo::OpDesc* h_desc = nullptr;     // pinned
     int *d_cta = nullptr, *h_cta = nullptr;   // [3][grid cap]: op, rank, then group [slots]

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) plan_chunk_kernel(OpDesc* descs, int nops
         d.c = min(d.m, d.n);
         d.L = d.n;
         d.jb = jacobi_block_rows(d.L, d.c, 8);
-        d.jb32 = jacobi_block_rows(d.L + d.c, d.c, 4);
+        d.jb32 = jacobi_block_rows_f32(d.L, d.c);
         if (jb_table) {   // autotuned rows per block of this (chi_l, chi_r) class
             const int* t = jb_table + ((size_t)d.cl * (chi_cap + 1) + d.cr) * 2;
             if (t[0] > 0) d.jb = t[0];

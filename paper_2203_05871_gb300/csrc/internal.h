@@ -119,6 +119,22 @@ __host__ __device__ inline int jacobi_block_rows(int rowlen, int c, int elem_byt
     while (b > 1 && b >= c) b >>= 1;
     return b;
 }
+// FP32 preconditioning pass: rows of at most kJacobiRegL elements take the
+// register path (one block of b <= kJacobiMaxB rows in shared memory, the
+// other in registers, the U32 part turned afterwards by the block pair's
+// accumulated rotation); longer rows the shared-memory path above.
+constexpr int kJacobiRegL = 1024;
+__host__ __device__ inline bool jacobi_f32_reg(int L) { return L <= kJacobiRegL; }
+__host__ __device__ inline int jacobi_block_rows_f32(int L, int c) {
+    if (!jacobi_f32_reg(L)) return jacobi_block_rows(L + c, c, 4);
+    int b = kJacobiMaxB;
+    while (b > 1 && b >= c) b >>= 1;
+    return b;
+}
+// whether b rows per block fit the FP32 pass for rows of length L (plus the c-long U32 part)
+__host__ __device__ inline bool jacobi_f32_fits(int b, int L, int c) {
+    return jacobi_f32_reg(L) ? b <= kJacobiMaxB : (size_t)2 * b * (L + c) * 4 <= (size_t)kJacobiRowBytes;
+}
 // block pairs per tournament round
 __host__ __device__ inline int jacobi_pairs_per_round(int c, int b) {
     const int nb = (c + b - 1) / b;

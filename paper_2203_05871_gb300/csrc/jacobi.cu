@@ -49,7 +49,8 @@ constexpr int JW = 8;             // warps per CTA
 constexpr int JT = JW * 32;
 constexpr int kRowBytes = kJacobiRowBytes;             // two blocks of rows in shared memory
 constexpr int kMaxB = kJacobiMaxB;
-constexpr int kSmemBytes = kRowBytes + 4 * kMaxB * 8;  // rows + norms (2b) + row ids
+constexpr int kSmemBytes = kRowBytes + 6 * kMaxB * 8;  // rows + norms (2b) + scales (2b) + row ids
+constexpr double kScaleFloor = 0x1p-32;   // FP64 row scales below this are multiplied into the row
 
 __device__ __forceinline__ int tour_player(int x, int step, int cp) {
     return x == 0 ? 0 : 1 + ((x - 1 + step) % (cp - 1));
@@ -77,6 +78,7 @@ template <typename T>
 struct Ctx {
     T* rows;          // [2b][rowlen] in shared memory
     T* nrm;           // [2b]
+    double* dsc;      // [2b] FP64 pass: the row is dsc times the stored row (scaled rotations)
     int* rid;         // [2b] global row index or -1
     unsigned* rho2;   // largest g^2 / (a b) rotated in this CTA and sweep (float bits)
     int rowlen, L;    // row length in smem (W part + Z part), W part length
@@ -118,6 +120,62 @@ __device__ __forceinline__ void rot_params(float a, float b, float g, float& cs,
     sn = cs * t;
 }
 
+// FP64 rotation on scaled rows (fast plane rotation with dynamic scaling,
+// Anda & Park 1994): the rows are w_p = d_p x_p, w_q = d_q x_q, and
+//   w_p' = cs w_p - sn w_q = (cs d_p) (x_p - t (d_q / d_p) x_q),
+//   w_q' = sn w_p + cs w_q = (cs d_q) (x_q + t (d_p / d_q) x_p),
+// so the stored rows take one FMA per element and the factor cs goes to the
+// scales.  |t| <= 1, so a scale shrinks by at most 1/sqrt(2) per rotation; a
+// scale below 2^-32 is multiplied into its row.  The kernel multiplies every
+// row by its scale after the last sweep.
+template <typename T>
+__device__ int scaled_rotate(const Ctx<T>& C, int p, int q, T* rp, T* rq, double a, double b, double g, double cs,
+                             double t, double dp, double dq, int lane) {
+    const double al = t * (dq / dp), be = t * (dp / dq);
+    int i = lane;
+    for (; i + 96 < C.rowlen; i += 128) {
+        double x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            x[u] = rp[i + 32 * u];
+            y[u] = rq[i + 32 * u];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            rp[i + 32 * u] = fma(-al, y[u], x[u]);
+            rq[i + 32 * u] = fma(be, x[u], y[u]);
+        }
+    }
+    for (; i < C.rowlen; i += 32) {
+        const double x = rp[i], y = rq[i];
+        rp[i] = fma(-al, y, x);
+        rq[i] = fma(be, x, y);
+    }
+    __syncwarp();
+    dp *= cs;
+    dq *= cs;
+    double na = fma(-t, g, a), nb = fma(t, g, b);
+    if (na < 0.1 * a) na = dp * dp * row_dot(rp, rp, C.L, lane);
+    if (nb < 0.1 * b) nb = dq * dq * row_dot(rq, rq, C.L, lane);
+    if (dp < kScaleFloor) {
+        for (int k = lane; k < C.rowlen; k += 32) rp[k] *= dp;
+        dp = 1.0;
+    }
+    if (dq < kScaleFloor) {
+        for (int k = lane; k < C.rowlen; k += 32) rq[k] *= dq;
+        dq = 1.0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        C.nrm[p] = na;
+        C.nrm[q] = nb;
+        C.dsc[p] = dp;
+        C.dsc[q] = dq;
+    }
+    __syncwarp();
+    return 1;
+}
+
 // One warp: rows p, q (shared-memory slots).  Returns 1 if it rotated.
 template <typename T>
 __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
@@ -139,7 +197,8 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         __syncwarp();
         return 0;
     }
-    const T g = row_dot(rp, rq, C.L, lane);
+    T g = row_dot(rp, rq, C.L, lane);
+    if constexpr (sizeof(T) == 8) g *= C.dsc[p] * C.dsc[q];
     // |g| <= tol sqrt(a b), written without squares of squares: in FP32, g^2
     // and a b underflow for rows below ~1e-10 of the largest, and those pairs
     // would pass as converged without ever being rotated
@@ -152,6 +211,7 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     rot_params(a, b, g, cs, sn, t);
     if (t == T(0)) return 0;
     if (lane == 0) atomicMax(C.rho2, __float_as_uint((float)(g / a * (g / b))));
+    if constexpr (sizeof(T) == 8) return scaled_rotate(C, p, q, rp, rq, a, b, g, cs, t, C.dsc[p], C.dsc[q], lane);
     int i = lane;
     for (; i + 96 < C.rowlen; i += 128) {
         T x[4], y[4];
@@ -302,6 +362,297 @@ __device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, 
     return rot;
 }
 
+// ---------------------------------------------------------------------------
+// FP32 pass, register path (W rows of at most kJacobiRegL elements).
+//
+// A block pair holds 2b <= 64 rows.  Block 0's W rows live in registers (warp w
+// holds slots w, w + JW, w + 2 JW, w + 3 JW), block 1's in shared memory.  In
+// cross step t warp w meets partner q = (t + w) mod b: it loads that row once,
+// rotates it against each of its own rows in registers and stores it once, so
+// a cross pair costs 2L/4 shared-memory accesses instead of the ~5L of the
+// shared-memory path.  The U32 rows take no part in the inner products: every
+// rotation of rows (p, q) is applied to rows (p, q) of a 64 x 64 accumulator
+// M (identity at the start of the block pair), and at the end the 2b U32 rows
+// are replaced by M times themselves, one column per thread.  The rotations
+// and their tests are those of the pointwise method.
+constexpr int kRegL = kJacobiRegL / 32;   // W elements per lane per row
+constexpr int kRegRows = kMaxB / JW;      // block-0 rows per warp
+constexpr int kM = 2 * kMaxB;             // accumulator dimension
+constexpr int kSmemReg = kJacobiRegL * kMaxB * 4 + kM * kM * 4 + kM * 8;
+constexpr int kSmemF32 = kSmemReg > kSmemBytes ? kSmemReg : kSmemBytes;
+static_assert(kRegRows * JW == kMaxB, "block 0 must fit the warps' registers");
+
+struct RegCtx {
+    float* rows;      // [b][L]: the W rows of the block in shared memory
+    float* M;         // [kM][kM]: accumulated rotation of the block pair's rows (row-major)
+    float* nrm;       // [2b]: squared norms (slot s of block k at k b + s)
+    int* rid;         // [2b]: global row index or -1
+    unsigned* rho2;   // largest g^2 / (a b) rotated in this CTA and sweep (float bits)
+    int b, L;
+    float floor2, tol;
+};
+
+__device__ __forceinline__ void rotate_m(const RegCtx& C, int ip, int iq, float cs, float sn, int lane) {
+    float* mp = C.M + ip * kM;
+    float* mq = C.M + iq * kM;
+#pragma unroll
+    for (int j = lane; j < kM; j += 32) {
+        const float x = mp[j], y = mq[j];
+        mp[j] = fmaf(cs, x, -sn * y);
+        mq[j] = fmaf(sn, x, cs * y);
+    }
+}
+
+// One warp: shared-memory slots p < q of the block whose rows sit at
+// accumulator offset mo.  Returns 1 if it rotated.
+__device__ int intra_pair_reg(const RegCtx& C, int p, int q, int mo, int lane) {
+    const int ip = mo + p, iq = mo + q;
+    if (C.rid[ip] < 0 || C.rid[iq] < 0) return 0;
+    float* rp = C.rows + (size_t)p * C.L;
+    float* rq = C.rows + (size_t)q * C.L;
+    const float a = C.nrm[ip], b = C.nrm[iq];
+    if (a <= C.floor2 || b <= C.floor2) {
+        if (a <= C.floor2 && a != 0.0f) {
+            for (int i = lane; i < C.L; i += 32) rp[i] = 0.0f;
+            __syncwarp();
+            if (lane == 0) C.nrm[ip] = 0.0f;
+        }
+        if (b <= C.floor2 && b != 0.0f) {
+            for (int i = lane; i < C.L; i += 32) rq[i] = 0.0f;
+            __syncwarp();
+            if (lane == 0) C.nrm[iq] = 0.0f;
+        }
+        __syncwarp();
+        return 0;
+    }
+    const float g = row_dot(rp, rq, C.L, lane);
+    if (g == 0.0f || fabsf(g) <= C.tol * sqrtf(a) * sqrtf(b)) return 0;
+    float cs, sn, t;
+    rot_params(a, b, g, cs, sn, t);
+    if (t == 0.0f) return 0;
+    if (lane == 0) atomicMax(C.rho2, __float_as_uint(g / a * (g / b)));
+    for (int i = lane; i < C.L; i += 32) {
+        const float x = rp[i], y = rq[i];
+        rp[i] = fmaf(cs, x, -sn * y);
+        rq[i] = fmaf(sn, x, cs * y);
+    }
+    rotate_m(C, ip, iq, cs, sn, lane);
+    __syncwarp();
+    float na = fmaf(-t, g, a), nb = fmaf(t, g, b);
+    if (na < 0.1f * a) na = row_dot(rp, rp, C.L, lane);
+    if (nb < 0.1f * b) nb = row_dot(rq, rq, C.L, lane);
+    if (lane == 0) {
+        C.nrm[ip] = na;
+        C.nrm[iq] = nb;
+    }
+    __syncwarp();
+    return 1;
+}
+
+// All pairs inside the block held in shared memory (circle method).
+__device__ int intra_block_reg(const RegCtx& C, int mo, int warp, int lane) {
+    const int b = C.b;
+    if (b < 2) return 0;
+    int rot = 0;
+    const int bp = b + (b & 1);
+    for (int t = 0; t < bp - 1; ++t) {
+        for (int x = warp; x < bp / 2; x += JW) {
+            const int P = tour_player(x, t, bp), Q = tour_player(bp - 1 - x, t, bp);
+            if (P >= b || Q >= b) continue;
+            rot += intra_pair_reg(C, min(P, Q), max(P, Q), mo, lane);
+        }
+        __syncthreads();
+    }
+    return rot;
+}
+
+// Loads the W rows of block `blk_slot0` (accumulator slots s0 .. s0 + b - 1)
+// into the shared-memory rows.
+__device__ __forceinline__ void load_block_reg(const RegCtx& C, const float* W, int ld, int s0, int warp, int lane) {
+    for (int s = warp; s < C.b; s += JW) {
+        const int row = C.rid[s0 + s];
+        if (row < 0) continue;
+        const float* w = W + (size_t)row * ld;
+        float* dst = C.rows + (size_t)s * C.L;
+        for (int k = lane; k < C.L; k += 32) dst[k] = __ldcg(w + k);
+    }
+}
+
+// One block pair of the register path: load, intra pairs (first round of a
+// sweep), cross pairs, store, U32 update.  Returns this warp's rotations.
+__device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c, int nb, const int bl[2],
+                              bool intra, double* snorm, int warp, int lane) {
+    __shared__ int s_any;
+    const int b = C.b, L = C.L;
+    int rot = 0;
+    for (int i = threadIdx.x; i < kM * kM; i += JT) C.M[i] = (i / kM == i % kM) ? 1.0f : 0.0f;
+    if (threadIdx.x == 0) s_any = 0;
+    if (threadIdx.x < 2 * b) {
+        const int s = threadIdx.x;
+        const int blk = bl[s / b];
+        const int row = blk * b + (s % b);
+        const bool ok = blk < nb && row < c;
+        C.rid[s] = ok ? row : -1;
+        C.nrm[s] = ok ? (float)__ldcg(snorm + row) : 0.0f;
+    }
+    __syncthreads();
+    // block 0 through shared memory into registers
+    load_block_reg(C, W, ld, 0, warp, lane);
+    __syncthreads();
+    if (intra) rot += intra_block_reg(C, 0, warp, lane);
+    float x[kRegRows][kRegL];
+    float ar[kRegRows];
+#pragma unroll
+    for (int r = 0; r < kRegRows; ++r) {
+        const int s = r * JW + warp;
+        const bool own = s < b && C.rid[s] >= 0;
+        ar[r] = own ? C.nrm[s] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < kRegL; ++u) {
+            const int e = u * 32 + lane;
+            x[r][u] = (own && e < L) ? C.rows[(size_t)s * L + e] : 0.0f;
+        }
+    }
+    __syncthreads();
+    // block 1 into shared memory
+    load_block_reg(C, W, ld, b, warp, lane);
+    __syncthreads();
+    if (intra) rot += intra_block_reg(C, b, warp, lane);
+    // cross pairs: at step t the warps meet distinct partners q = (t + warp) mod b
+    for (int t = 0; t < b; ++t) {
+        const int q = (t + warp) % b;
+        if (warp < b && C.rid[b + q] >= 0) {
+            float* rq = C.rows + (size_t)q * L;
+            float y[kRegL];
+#pragma unroll
+            for (int u = 0; u < kRegL; ++u) {
+                const int e = u * 32 + lane;
+                y[u] = e < L ? rq[e] : 0.0f;
+            }
+            float bq = C.nrm[b + q];
+            bool ymod = false;
+#pragma unroll
+            for (int r = 0; r < kRegRows; ++r) {
+                const int s = r * JW + warp;
+                if (s >= b || C.rid[s] < 0) continue;
+                const float a = ar[r];
+                if (a <= C.floor2 || bq <= C.floor2) {
+                    if (a <= C.floor2 && a != 0.0f) {
+#pragma unroll
+                        for (int u = 0; u < kRegL; ++u) x[r][u] = 0.0f;
+                        ar[r] = 0.0f;
+                    }
+                    if (bq <= C.floor2 && bq != 0.0f) {
+#pragma unroll
+                        for (int u = 0; u < kRegL; ++u) y[u] = 0.0f;
+                        bq = 0.0f;
+                        ymod = true;
+                    }
+                    continue;
+                }
+                float g0 = 0.0f, g1 = 0.0f;
+#pragma unroll
+                for (int u = 0; u < kRegL; u += 2) {
+                    g0 = fmaf(x[r][u], y[u], g0);
+                    g1 = fmaf(x[r][u + 1], y[u + 1], g1);
+                }
+                const float g = warp_sum(g0 + g1);
+                if (g == 0.0f || fabsf(g) <= C.tol * sqrtf(a) * sqrtf(bq)) continue;
+                float cs, sn, tt;
+                rot_params(a, bq, g, cs, sn, tt);
+                if (tt == 0.0f) continue;
+                if (lane == 0) atomicMax(C.rho2, __float_as_uint(g / a * (g / bq)));
+#pragma unroll
+                for (int u = 0; u < kRegL; ++u) {
+                    const float xv = x[r][u], yv = y[u];
+                    x[r][u] = fmaf(cs, xv, -sn * yv);
+                    y[u] = fmaf(sn, xv, cs * yv);
+                }
+                rotate_m(C, s, b + q, cs, sn, lane);
+                float na = fmaf(-tt, g, a), nq = fmaf(tt, g, bq);
+                if (na < 0.1f * a) {
+                    float s0 = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < kRegL; ++u) s0 = fmaf(x[r][u], x[r][u], s0);
+                    na = warp_sum(s0);
+                }
+                if (nq < 0.1f * bq) {
+                    float s0 = 0.0f;
+#pragma unroll
+                    for (int u = 0; u < kRegL; ++u) s0 = fmaf(y[u], y[u], s0);
+                    nq = warp_sum(s0);
+                }
+                ar[r] = na;
+                bq = nq;
+                ymod = true;
+                ++rot;
+            }
+            if (ymod) {
+#pragma unroll
+                for (int u = 0; u < kRegL; ++u) {
+                    const int e = u * 32 + lane;
+                    if (e < L) rq[e] = y[u];
+                }
+                __syncwarp();
+                if (lane == 0) C.nrm[b + q] = bq;
+            }
+        }
+        __syncthreads();
+    }
+    // store: block 0 from registers, block 1 from shared memory
+#pragma unroll
+    for (int r = 0; r < kRegRows; ++r) {
+        const int s = r * JW + warp;
+        if (s >= b || C.rid[s] < 0) continue;
+        float* w = W + (size_t)C.rid[s] * ld;
+#pragma unroll
+        for (int u = 0; u < kRegL; ++u) {
+            const int e = u * 32 + lane;
+            if (e < L) __stcg(w + e, x[r][u]);
+        }
+        if (lane == 0) __stcg(snorm + C.rid[s], (double)ar[r]);
+    }
+    for (int s = warp; s < b; s += JW) {
+        const int row = C.rid[b + s];
+        if (row < 0) continue;
+        const float* src = C.rows + (size_t)s * L;
+        float* w = W + (size_t)row * ld;
+        for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
+        if (lane == 0) __stcg(snorm + row, (double)C.nrm[b + s]);
+    }
+    if (lane == 0 && rot > 0) atomicOr(&s_any, 1);
+    __syncthreads();
+    // U32 rows <- M U32 rows, one column per thread (M's rows and columns past
+    // 2b are unit vectors; z is 0 there)
+    if (s_any) {
+        for (int k = threadIdx.x; k < c; k += JT) {
+            float z[kM];
+#pragma unroll
+            for (int j = 0; j < kM; ++j) {
+                const int row = j < 2 * b ? C.rid[j] : -1;
+                z[j] = row >= 0 ? __ldcg(Z + (size_t)row * ld + k) : 0.0f;
+            }
+            for (int i = 0; i < 2 * b; ++i) {
+                const int row = C.rid[i];
+                if (row < 0) continue;
+                const float4* m4 = reinterpret_cast<const float4*>(C.M + i * kM);
+                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+#pragma unroll
+                for (int j4 = 0; j4 < kM / 4; ++j4) {
+                    const float4 m = m4[j4];
+                    s0 = fmaf(m.x, z[4 * j4], s0);
+                    s1 = fmaf(m.y, z[4 * j4 + 1], s1);
+                    s2 = fmaf(m.z, z[4 * j4 + 2], s2);
+                    s3 = fmaf(m.w, z[4 * j4 + 3], s3);
+                }
+                __stcg(Z + (size_t)row * ld + k, (s0 + s1) + (s2 + s3));
+            }
+        }
+    }
+    __syncthreads();
+    return rot;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
@@ -315,7 +666,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     const OpDesc& d = descs[op];
     unsigned* sw = sync + (size_t)op * kSyncWords;
     const int c = d.c, L = d.L;
-    const int b = kF32 ? d.jb32 : d.jb;
+    int b = kF32 ? d.jb32 : d.jb;
     T* W;
     T* Z;
     if constexpr (kF32) {
@@ -326,6 +677,16 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         Z = d.transposed ? d.Z : nullptr;
     }
     const int zl = Z ? c : 0;
+    // a block size that does not fit shared memory (or the registers) is a
+    // planning error: every CTA of the op sees it and returns at once
+    if (b < 1 || b > kMaxB ||
+        ((!kF32 || !jacobi_f32_reg(L)) && (size_t)2 * b * (L + zl) * sizeof(T) > (size_t)kRowBytes)) {
+        if (threadIdx.x == 0) atomicOr(d.status, (int)MPDO_ST_CAPACITY);
+        return;
+    }
+    // the same value, read again so that the range the check proves does not
+    // reach the register allocation of the FP32 paths (it made them spill)
+    b = *(volatile const int*)(kF32 ? &d.jb32 : &d.jb);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned gen = 0;
     __shared__ double s_floor2, s_scale;
@@ -337,7 +698,9 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     C.L = L;
     C.rows = reinterpret_cast<T*>(smem_raw);
     C.nrm = C.rows + (size_t)2 * b * C.rowlen;
-    C.rid = reinterpret_cast<int*>(C.nrm + 2 * b);
+    C.dsc = reinterpret_cast<double*>(C.nrm + 2 * b);
+    C.rid = reinterpret_cast<int*>(C.dsc + 2 * b);
+    double* dscale = d.snorm + ld;   // FP64 pass: per-row scales (the QR's column norms are dead here)
     C.rho2 = &s_rho2;
     {
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
@@ -355,7 +718,10 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
             a = fma(x, x, a);
         }
         a = warp_sum(a);
-        if (lane == 0) __stcg(d.snorm + row, a);
+        if (lane == 0) {
+            __stcg(d.snorm + row, a);
+            if constexpr (!kF32) __stcg(dscale + row, 1.0);
+        }
     }
     if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
     if (threadIdx.x == 0) {
@@ -389,6 +755,17 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     C.floor2 = (T)(kF32 ? s_floor2 * s_scale * s_scale : s_floor2);
     if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
     {
+        const bool reg = kF32 && jacobi_f32_reg(L);
+        RegCtx RC;
+        RC.rows = reinterpret_cast<float*>(smem_raw);
+        RC.M = reinterpret_cast<float*>(smem_raw + (size_t)kJacobiRegL * kMaxB * 4);
+        RC.nrm = RC.M + kM * kM;
+        RC.rid = reinterpret_cast<int*>(RC.nrm + kM);
+        RC.rho2 = &s_rho2;
+        RC.b = b;
+        RC.L = L;
+        RC.floor2 = (float)C.floor2;
+        RC.tol = (float)C.tol;
         const int nb = (c + b - 1) / b;
         const int nbp = nb + (nb & 1);
         const int npair = nbp / 2;
@@ -407,6 +784,10 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                     a = fma(x, x, a);
                 }
                 a = warp_sum(a);
+                if constexpr (!kF32) {
+                    const double dv = __ldcg(dscale + row);
+                    a = a * dv * dv;
+                }
                 if (lane == 0) __stcg(d.snorm + row, (double)a);
             }
             if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
@@ -414,6 +795,12 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                 for (int i = g; i < npair; i += G) {
                     const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
                     const int bl[2] = {P < Q ? P : Q, P < Q ? Q : P};
+                    if constexpr (kF32) {
+                        if (reg) {
+                            rot += block_pair_reg(RC, W, Z, ld, c, nb, bl, r == 0, d.snorm, warp, lane);
+                            continue;
+                        }
+                    }
                     // load the two blocks (slot s < b: block bl[0]; s >= b: block bl[1])
                     for (int s = warp; s < 2 * b; s += JW) {
                         const int blk = bl[s / b];
@@ -429,10 +816,12 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                             const T nv = (T)__ldcg(d.snorm + row);
                             if (lane == 0) {
                                 C.nrm[s] = nv;
+                                if constexpr (!kF32) C.dsc[s] = __ldcg(dscale + row);
                                 C.rid[s] = row;
                             }
                         } else if (lane == 0) {
                             C.nrm[s] = T(0);
+                            if constexpr (!kF32) C.dsc[s] = 1.0;
                             C.rid[s] = -1;
                         }
                     }
@@ -447,7 +836,10 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                         for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
                         if (Z)
                             for (int k = lane; k < c; k += 32) __stcg(Z + (size_t)row * ld + k, src[L + k]);
-                        if (lane == 0) __stcg(d.snorm + row, (double)C.nrm[s]);
+                        if (lane == 0) {
+                            __stcg(d.snorm + row, (double)C.nrm[s]);
+                            if constexpr (!kF32) __stcg(dscale + row, C.dsc[s]);
+                        }
                     }
                     __syncthreads();
                 }
@@ -459,16 +851,28 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                 if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             }
             // FP32 pass: done when fewer than c/4 pairs still rotate (a few pairs
-            // sit at FP32's resolution forever; the FP64 pass finishes them)
-            // FP64: also converged when the largest relative off-orthogonality rotated
-            // away was below 1e-10: the next sweep would meet pairs at ~1e-20, far
-            // under tol, and rotate nothing
+            // sit at FP32's resolution forever; the FP64 pass finishes them), or
+            // when the largest relative off-orthogonality rotated away was at most
+            // 1e-3: the rows are then orthogonal to ~1e-6, FP32's rounding level
+            // for these inner products, and further sweeps only chase rounding.
+            // FP64: no rotation, or the largest rotated was below 1e-10: the next
+            // sweep would meet pairs at ~1e-20, far under tol, and rotate nothing
             if (threadIdx.x == 0)
                 s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u)) ||
-                         (!kF32 && __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= 1e-20f);
+                         (__uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= (kF32 ? 1e-6f : 1e-20f));
             __syncthreads();
             conv = s_conv;
             used = sweep + 1;
+        }
+        if constexpr (!kF32) {   // rows out of their scales (the last round ended with a barrier)
+            for (int row = g * JW + warp; row < c; row += G * JW) {
+                const double dv = __ldcg(dscale + row);
+                if (dv == 1.0) continue;
+                T* w = W + (size_t)row * ld;
+                for (int i = lane; i < L; i += 32) __stcg(w + i, __ldcg(w + i) * dv);
+                if (Z)
+                    for (int i = lane; i < c; i += 32) __stcg(Z + (size_t)row * ld + i, __ldcg(Z + (size_t)row * ld + i) * dv);
+            }
         }
         if (g == 0 && threadIdx.x == 0) {
             if (!kF32) {
@@ -499,12 +903,12 @@ cudaError_t jacobi_max_resident(int* blocks) {
     if ((e = cudaFuncSetAttribute(jacobi_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes)) !=
+    if ((e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF32)) !=
         cudaSuccess)
         return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, jacobi_kernel<double>, JT, kSmemBytes)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, jacobi_kernel<float>, JT, kSmemBytes)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, jacobi_kernel<float>, JT, kSmemF32)) != cudaSuccess)
         return e;
     *blocks = sms * (per64 < per32 ? per64 : per32);
     return cudaSuccess;
@@ -518,7 +922,7 @@ cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, c
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
                     (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
     const void* fn = fp32 ? (const void*)jacobi_kernel<float> : (const void*)jacobi_kernel<double>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(JT), args, kSmemBytes, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(JT), args, fp32 ? kSmemF32 : kSmemBytes, st);
 }
 
 }  // namespace mpdo

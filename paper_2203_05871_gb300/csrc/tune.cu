@@ -1,8 +1,9 @@
 // Autotuner of the Jacobi SVD's rows per block, per (chi_l, chi_r) class
 // (mpdo_autotune).
 //
-// The one-sided Jacobi stages two blocks of b rows in shared memory per block
-// pair (jacobi.cu).  Larger blocks mean fewer rounds and barriers per sweep and
+// The one-sided Jacobi stages two blocks of b rows per block pair (jacobi.cu:
+// both in shared memory, or for the FP32 pass on rows of at most 1024
+// elements one in shared memory and one in registers).  Larger blocks mean fewer rounds and barriers per sweep and
 // more work per shared-memory load; smaller ones more block pairs per round,
 // i.e. more CTAs per op.  The best b depends on the row length, the number of
 // rows and how many ops share the GPU, so it is measured: for every class the
@@ -123,12 +124,12 @@ extern "C" int mpdo_autotune(mpdo_ctx* c, const int* classes, int n_classes, int
         }
         for (int pass = 0; pass < (c->mixed ? 2 : 1); ++pass) {
             const bool fp32 = pass == 1;
-            const int rowlen = fp32 ? n + cc : n;
-            const int eb = fp32 ? 4 : 8;
+            const int rowlen = n;
+            const int eb = 8;
             double best = 1e300;
-            int best_b = fp32 ? jacobi_block_rows(rowlen, cc, eb) : jacobi_block_rows(rowlen, cc, eb);
+            int best_b = fp32 ? jacobi_block_rows_f32(n, cc) : jacobi_block_rows(rowlen, cc, eb);
             for (int b = 1; b <= kJacobiMaxB; b *= 2) {
-                if ((size_t)2 * b * rowlen * eb > (size_t)kJacobiRowBytes) break;
+                if (fp32 ? !jacobi_f32_fits(b, n, cc) : (size_t)2 * b * rowlen * eb > (size_t)kJacobiRowBytes) break;
                 if (b > 1 && b >= cc) break;
                 if (fp32) {   // the FP32 pass starts from the FP64 rows of W0
                     for (auto& d : h) d.jb = jacobi_block_rows(n, cc, 8);

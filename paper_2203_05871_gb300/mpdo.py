@@ -82,6 +82,9 @@ def load_library(path: str = LIB_PATH):
                                              ctypes.c_int]),
         "mpdo_profile_sweeps": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong),
                                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "mpdo_profile_sweeps_critical": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_longlong),
+                                                        ctypes.POINTER(ctypes.c_longlong),
+                                                        ctypes.POINTER(ctypes.c_longlong)]),
         "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
@@ -106,7 +109,7 @@ def exported_symbols() -> list[str]:
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
-            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -300,6 +303,9 @@ class Solver:
     def profile_read(self, reset: bool = False):
         sw, sv, s32 = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
         _check(self._lib.mpdo_profile_sweeps(self._h, ctypes.byref(sw), ctypes.byref(sv), ctypes.byref(s32)))
+        cr, cr32, nch = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(self._lib.mpdo_profile_sweeps_critical(self._h, ctypes.byref(cr), ctypes.byref(cr32),
+                                                      ctypes.byref(nch)))
         K = len(PROFILE_KINDS)
         ms = np.zeros(K)
         ln = np.zeros(K, np.int64)
@@ -311,6 +317,9 @@ class Solver:
         out["jacobi_svd"]["sweeps"] = int(sw.value)
         out["jacobi_svd"]["svds"] = int(sv.value)
         out["jacobi_svd"]["sweeps_fp32"] = int(s32.value)
+        out["jacobi_svd"]["critical_sweeps"] = int(cr.value)
+        out["jacobi_svd"]["critical_sweeps_fp32"] = int(cr32.value)
+        out["jacobi_svd"]["chunks"] = int(nch.value)
         return out
 
     def rank_log(self, n_steps: int):

@@ -252,6 +252,31 @@ def test_mixed_chi256_one_step_sampled(decay, tol):
     assert np.all(np.abs(g - rg) <= tol * np.maximum(1.0, scale))
 
 
+def test_mixed_long_rows_chi300():
+    """Rows longer than 1024: on an N=11 chain with a 300-wide bond 6 between
+    16-wide bonds, the first layer's op on sites (4, 5) has 64 rows of
+    4 * 300 = 1200 and takes the FP32 pass's shared-memory path; the other ops
+    take its register path.  One step against the oracle at the GPU's ranks."""
+    n = 11
+    dims = [1, 4, 16, 16, 16, 16, 300, 16, 16, 16, 4, 1]
+    tens = W.random_mpo_tensors(dims, seed=13, decay=0.02)
+    wl = W.uniform_model("chain11_chi300", n, W.chain_bonds(n), chi_max=300, cutoff=1e-10, dt=0.02)
+    s = solver_for(wl, chi_cap=300, precision=_mixed())
+    s.set_state(0, dims, tens)
+    s.step(1)
+    assert s.status()["status"][0] == 0
+    log = [int(k) for k in s.rank_log(1)[0]]
+    st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
+    o = tebd.TEBD(wl, 0, state=st)
+    o.run(1, forced_k=log)
+    gz, rz = s.measure_1q(range(n), "Z")[0], o.z()
+    assert np.all(np.abs(gz - rz) <= TOL_MIXED * np.maximum(1.0, np.abs(rz)))
+    pairs = [(0, 10), (3, 6), (4, 5), (5, 6)]
+    g, rg = s.measure_2q(pairs, "ZZ", connected=True)[0], o.zz_connected(pairs)
+    scale = np.array([abs(o.state.expect_2q(i, j)) + abs(rz[i] * rz[j]) for (i, j) in pairs])
+    assert np.all(np.abs(g - rg) <= TOL_MIXED * np.maximum(1.0, scale))
+
+
 def test_mixed_vs_fp64_per_observable_error():
     """Precision comparison (N=20 chain, seeded couplings): the mixed path
     (3xTF32 tensor-core contractions, FP32-preconditioned FP64 SVD) against the

@@ -236,17 +236,24 @@ def random_mpo_state(n: int, chi: int, seed: int, decay: float = 0.0):
     decay > 0 grades the bonds the way time-evolved states are graded (their
     Schmidt values fall off).  Used to start a benchmark at saturated bond
     dimension.  Returns (dims, tensors)."""
-    rng = np.random.Generator(np.random.PCG64(seed))
     dims = [1]
     for p in range(n - 1):
         dims.append(int(min(chi, 4 ** min(p + 1, n - p - 1))))
     dims.append(1)
+    return dims, random_mpo_tensors(dims, seed, decay)
+
+
+def random_mpo_tensors(dims, seed: int, decay: float = 0.0):
+    """Site tensors of random_mpo_state for given bond dimensions dims[0..n]
+    (dims[0] = dims[n] = 1; the caller keeps them within the 4^min(p, n-p)
+    bound)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
     tensors = []
-    for p in range(n):
+    for p in range(len(dims) - 1):
         cl, cr = dims[p], dims[p + 1]
         scale = np.exp(-decay * np.arange(cr)) if decay > 0 else np.ones(cr)
         tensors.append(rng.standard_normal((cl, 4, cr)) / np.sqrt(4.0 * cl) * scale[None, None, :])
-    return dims, tensors
+    return tensors
 
 
 ALL = {
