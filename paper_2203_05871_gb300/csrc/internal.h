@@ -107,7 +107,6 @@ struct JacobiPlan {
     int grid;            // total CTAs (cooperative)
     int max_resident;    // co-resident capacity
 };
-int jacobi_threads();
 constexpr int kJacobiRowBytes = 128 * 1024;   // shared memory for the two row blocks of a pair
 constexpr int kJacobiMaxB = 32;               // rows per block at most
 constexpr int kQrWarps = 8;                   // warps per QR CTA

@@ -45,8 +45,13 @@ namespace mpdo {
 
 namespace {
 
-constexpr int JW = 8;             // warps per CTA
-constexpr int JT = JW * 32;
+// warps per CTA: the FP32 pass is latency-bound and runs 16 warps (at most 128
+// registers each; measured on the chi = 256 chain: 129 ms per step with 8 warps,
+// 117 with 12, 104 with 16); the FP64 pass keeps 8 (its blocks of 8 rows feed 8 warps)
+template <typename T>
+constexpr int kWarps = sizeof(T) == 4 ? 16 : 8;
+template <typename T>
+constexpr int kThreads = kWarps<T> * 32;
 constexpr int kRowBytes = kJacobiRowBytes;             // two blocks of rows in shared memory
 constexpr int kMaxB = kJacobiMaxB;
 constexpr int kSmemBytes = kRowBytes + 6 * kMaxB * 8;  // rows + norms (2b) + scales (2b) + row ids
@@ -243,97 +248,6 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     return 1;
 }
 
-// Cross pairs of the FP32 pass with one block-0 row per warp (b <= JW): warp
-// w keeps row w in registers while the b rows of block 1 pass by, so each
-// rotation reads and writes only the partner row in shared memory (the pass
-// is bound by shared-memory bandwidth, not by FP32 arithmetic).
-constexpr int kRegU = 64;   // row elements per lane held in registers (rows <= 2048)
-
-__device__ int cross_pairs_in_registers(const Ctx<float>& C, int b, int warp, int lane) {
-    float x[kRegU];
-    const bool own = warp < b && C.rid[warp] >= 0;
-    float a = 0.0f;
-    if (own) {
-        const float* rp = C.rows + (size_t)warp * C.rowlen;
-#pragma unroll
-        for (int u = 0; u < kRegU; ++u) {
-            const int e = u * 32 + lane;
-            x[u] = e < C.rowlen ? rp[e] : 0.0f;
-        }
-        a = C.nrm[warp];
-    }
-    int rot = 0;
-    for (int t = 0; t < b; ++t) {
-        const int q = b + (warp + t) % b;
-        if (own && C.rid[q] >= 0) {
-            float* rq = C.rows + (size_t)q * C.rowlen;
-            const float bq = C.nrm[q];
-            if (a <= C.floor2 || bq <= C.floor2) {
-                if (a <= C.floor2 && a != 0.0f) {
-#pragma unroll
-                    for (int u = 0; u < kRegU; ++u) x[u] = 0.0f;
-                    a = 0.0f;
-                }
-                if (bq <= C.floor2 && bq != 0.0f) {
-                    for (int i = lane; i < C.L; i += 32) rq[i] = 0.0f;
-                    __syncwarp();
-                    if (lane == 0) C.nrm[q] = 0.0f;
-                }
-            } else {
-                float g0 = 0.0f, g1 = 0.0f;
-#pragma unroll
-                for (int u = 0; u < kRegU; u += 2) {
-                    const int e0 = u * 32 + lane, e1 = e0 + 32;
-                    if (e0 < C.L) g0 = fmaf(x[u], rq[e0], g0);
-                    if (e1 < C.L) g1 = fmaf(x[u + 1], rq[e1], g1);
-                }
-                const float g = warp_sum(g0 + g1);
-                if (g != 0.0f && fabsf(g) > C.tol * sqrtf(a) * sqrtf(bq)) {
-                    float cs, sn, tt;
-                    rot_params(a, bq, g, cs, sn, tt);
-                    if (tt != 0.0f) {
-#pragma unroll
-                        for (int u = 0; u < kRegU; ++u) {
-                            const int e = u * 32 + lane;
-                            if (e < C.rowlen) {
-                                const float y = rq[e];
-                                rq[e] = fmaf(sn, x[u], cs * y);
-                                x[u] = fmaf(cs, x[u], -sn * y);
-                            }
-                        }
-                        __syncwarp();
-                        float na = fmaf(-tt, g, a), nb = fmaf(tt, g, bq);
-                        if (na < 0.1f * a) {
-                            float s0 = 0.0f;
-#pragma unroll
-                            for (int u = 0; u < kRegU; ++u)
-                                if (u * 32 + lane < C.L) s0 = fmaf(x[u], x[u], s0);
-                            na = warp_sum(s0);
-                        }
-                        if (nb < 0.1f * bq) nb = row_dot(rq, rq, C.L, lane);
-                        a = na;
-                        if (lane == 0) C.nrm[q] = nb;
-                        ++rot;
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (own) {
-        float* rp = C.rows + (size_t)warp * C.rowlen;
-#pragma unroll
-        for (int u = 0; u < kRegU; ++u) {
-            const int e = u * 32 + lane;
-            if (e < C.rowlen) rp[e] = x[u];
-        }
-        __syncwarp();
-        if (lane == 0) C.nrm[warp] = a;
-    }
-    __syncthreads();
-    return rot;
-}
-
 // All pairs inside each of the two blocks (circle method, first round of a
 // sweep only), then all cross pairs between the two blocks.
 template <typename T>
@@ -342,7 +256,7 @@ __device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, 
     if (intra && b > 1) {
         const int bp = b + (b & 1);
         for (int t = 0; t < bp - 1; ++t) {
-            for (int x = warp; x < bp; x += JW) {   // x < bp/2: block 0, else block 1
+            for (int x = warp; x < bp; x += kWarps<T>) {   // x < bp/2: block 0, else block 1
                 const int blk = x < bp / 2 ? 0 : 1;
                 const int y = x % (bp / 2);
                 const int P = tour_player(y, t, bp), Q = tour_player(bp - 1 - y, t, bp);
@@ -352,11 +266,8 @@ __device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, 
             __syncthreads();
         }
     }
-    if constexpr (sizeof(T) == 4) {
-        if (b <= JW && C.rowlen <= 32 * kRegU) return rot + cross_pairs_in_registers(C, b, warp, lane);
-    }
     for (int t = 0; t < b; ++t) {
-        for (int i = warp; i < b; i += JW) rot += pair_rotate(C, i, b + (i + t) % b, lane);
+        for (int i = warp; i < b; i += kWarps<T>) rot += pair_rotate(C, i, b + (i + t) % b, lane);
         __syncthreads();
     }
     return rot;
@@ -366,31 +277,55 @@ __device__ int process_block_pair(const Ctx<T>& C, int b, bool intra, int warp, 
 // FP32 pass, register path (W rows of at most kJacobiRegL elements).
 //
 // A block pair holds 2b <= 64 rows.  Block 0's W rows live in registers (warp w
-// holds slots w, w + JW, w + 2 JW, w + 3 JW), block 1's in shared memory.  In
-// cross step t warp w meets partner q = (t + w) mod b: it loads that row once,
-// rotates it against each of its own rows in registers and stores it once, so
-// a cross pair costs 2L/4 shared-memory accesses instead of the ~5L of the
-// shared-memory path.  The U32 rows take no part in the inner products: every
-// rotation of rows (p, q) is applied to rows (p, q) of a 64 x 64 accumulator
-// M (identity at the start of the block pair), and at the end the 2b U32 rows
-// are replaced by M times themselves, one column per thread.  The rotations
-// and their tests are those of the pointwise method.
+// of RW = 16 holds slots w and w + RW), block 1's in shared memory.  In cross
+// step t warp w meets partner q = (t + w) mod b: it loads that row once,
+// rotates it against its own rows in registers and stores it once.  The U32
+// rows take no part in the inner products: every rotation of rows (p, q) is
+// applied to rows (p, q) of a 64 x 64 accumulator M (identity at the start of
+// the block pair), and at the end the 2b U32 rows are replaced by M times
+// themselves, one column per thread.  The pass is latency-bound (one CTA per
+// SM), hence as many warps as the registers of the rows allow.
+//
+// Cross rotations act on scaled rows (fast plane rotations with dynamic
+// scaling, Anda & Park 1994): row p is d_p x_p, and
+//   x_p <- x_p - t (d_q / d_p) x_q,  x_q <- x_q + t (d_p / d_q) x_p,  d <- cs d,
+// one FMA per element instead of two multiplies and two FMAs.  The scales
+// start at 1 when a block pair is loaded and are multiplied in when it is
+// stored; a row meets at most b = 32 partners in between, and cs >= 1/sqrt(2),
+// so a scale stays above 2^-16.
+constexpr int RW = kWarps<float>;
+constexpr int RT = kThreads<float>;
 constexpr int kRegL = kJacobiRegL / 32;   // W elements per lane per row
-constexpr int kRegRows = kMaxB / JW;      // block-0 rows per warp
+constexpr int kRegRows = (kMaxB + RW - 1) / RW;   // block-0 rows per warp at most
 constexpr int kM = 2 * kMaxB;             // accumulator dimension
-constexpr int kSmemReg = kJacobiRegL * kMaxB * 4 + kM * kM * 4 + kM * 8;
+constexpr int kZT = 128;                  // U32 columns per tile of the accumulator product
+constexpr int kSmemReg = kJacobiRegL * kMaxB * 4 + kM * kM * 4 + kM * 12;
 constexpr int kSmemF32 = kSmemReg > kSmemBytes ? kSmemReg : kSmemBytes;
-static_assert(kRegRows * JW == kMaxB, "block 0 must fit the warps' registers");
+static_assert(kRegRows * RW >= kMaxB, "block 0 must fit the warps' registers");
+static_assert(RT == (kM / 4) * (kZT / 4), "one 4 x 4 output tile per thread");
+static_assert(kM * kZT + kM * kM <= kJacobiRegL * kMaxB, "U32 tile and M^T fit the rows' space");
 
 struct RegCtx {
     float* rows;      // [b][L]: the W rows of the block in shared memory
     float* M;         // [kM][kM]: accumulated rotation of the block pair's rows (row-major)
     float* nrm;       // [2b]: squared norms (slot s of block k at k b + s)
+    float* dsc;       // [b]: scales of block 1's rows during the cross pairs
     int* rid;         // [2b]: global row index or -1
     unsigned* rho2;   // largest g^2 / (a b) rotated in this CTA and sweep (float bits)
     int b, L;
     float floor2, tol;
 };
+
+// FP32 rotation parameters with the fast division (the angle only needs FP32
+// accuracy; 2g is never above 2^126 since the rows are scaled to unit mean
+// square norm)
+__device__ __forceinline__ void rot_params_fast(float a, float b, float g, float& cs, float& sn, float& t) {
+    const float zeta = __fdividef(b - a, 2.0f * g);
+    t = fabsf(zeta) > 1e18f ? __fdividef(0.5f, zeta)
+                            : __fdividef(copysignf(1.0f, zeta), fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.0f)));
+    cs = rsqrtf(fmaf(t, t, 1.0f));
+    sn = cs * t;
+}
 
 __device__ __forceinline__ void rotate_m(const RegCtx& C, int ip, int iq, float cs, float sn, int lane) {
     float* mp = C.M + ip * kM;
@@ -404,7 +339,7 @@ __device__ __forceinline__ void rotate_m(const RegCtx& C, int ip, int iq, float 
 }
 
 // One warp: shared-memory slots p < q of the block whose rows sit at
-// accumulator offset mo.  Returns 1 if it rotated.
+// accumulator offset mo (plain rotations).  Returns 1 if it rotated.
 __device__ int intra_pair_reg(const RegCtx& C, int p, int q, int mo, int lane) {
     const int ip = mo + p, iq = mo + q;
     if (C.rid[ip] < 0 || C.rid[iq] < 0) return 0;
@@ -428,7 +363,7 @@ __device__ int intra_pair_reg(const RegCtx& C, int p, int q, int mo, int lane) {
     const float g = row_dot(rp, rq, C.L, lane);
     if (g == 0.0f || fabsf(g) <= C.tol * sqrtf(a) * sqrtf(b)) return 0;
     float cs, sn, t;
-    rot_params(a, b, g, cs, sn, t);
+    rot_params_fast(a, b, g, cs, sn, t);
     if (t == 0.0f) return 0;
     if (lane == 0) atomicMax(C.rho2, __float_as_uint(g / a * (g / b)));
     for (int i = lane; i < C.L; i += 32) {
@@ -456,7 +391,7 @@ __device__ int intra_block_reg(const RegCtx& C, int mo, int warp, int lane) {
     int rot = 0;
     const int bp = b + (b & 1);
     for (int t = 0; t < bp - 1; ++t) {
-        for (int x = warp; x < bp / 2; x += JW) {
+        for (int x = warp; x < bp / 2; x += RW) {
             const int P = tour_player(x, t, bp), Q = tour_player(bp - 1 - x, t, bp);
             if (P >= b || Q >= b) continue;
             rot += intra_pair_reg(C, min(P, Q), max(P, Q), mo, lane);
@@ -466,10 +401,9 @@ __device__ int intra_block_reg(const RegCtx& C, int mo, int warp, int lane) {
     return rot;
 }
 
-// Loads the W rows of block `blk_slot0` (accumulator slots s0 .. s0 + b - 1)
-// into the shared-memory rows.
+// W rows of accumulator slots s0 .. s0 + b - 1 into the shared-memory rows
 __device__ __forceinline__ void load_block_reg(const RegCtx& C, const float* W, int ld, int s0, int warp, int lane) {
-    for (int s = warp; s < C.b; s += JW) {
+    for (int s = warp; s < C.b; s += RW) {
         const int row = C.rid[s0 + s];
         if (row < 0) continue;
         const float* w = W + (size_t)row * ld;
@@ -485,7 +419,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     __shared__ int s_any;
     const int b = C.b, L = C.L;
     int rot = 0;
-    for (int i = threadIdx.x; i < kM * kM; i += JT) C.M[i] = (i / kM == i % kM) ? 1.0f : 0.0f;
+    for (int i = threadIdx.x; i < kM * kM; i += RT) C.M[i] = (i / kM == i % kM) ? 1.0f : 0.0f;
     if (threadIdx.x == 0) s_any = 0;
     if (threadIdx.x < 2 * b) {
         const int s = threadIdx.x;
@@ -494,6 +428,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
         const bool ok = blk < nb && row < c;
         C.rid[s] = ok ? row : -1;
         C.nrm[s] = ok ? (float)__ldcg(snorm + row) : 0.0f;
+        if (s < b) C.dsc[s] = 1.0f;
     }
     __syncthreads();
     // block 0 through shared memory into registers
@@ -501,12 +436,13 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     __syncthreads();
     if (intra) rot += intra_block_reg(C, 0, warp, lane);
     float x[kRegRows][kRegL];
-    float ar[kRegRows];
+    float ar[kRegRows], dx[kRegRows];
 #pragma unroll
     for (int r = 0; r < kRegRows; ++r) {
-        const int s = r * JW + warp;
+        const int s = r * RW + warp;
         const bool own = s < b && C.rid[s] >= 0;
         ar[r] = own ? C.nrm[s] : 0.0f;
+        dx[r] = 1.0f;
 #pragma unroll
         for (int u = 0; u < kRegL; ++u) {
             const int e = u * 32 + lane;
@@ -529,11 +465,11 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
                 const int e = u * 32 + lane;
                 y[u] = e < L ? rq[e] : 0.0f;
             }
-            float bq = C.nrm[b + q];
+            float bq = C.nrm[b + q], dy = C.dsc[q];
             bool ymod = false;
 #pragma unroll
             for (int r = 0; r < kRegRows; ++r) {
-                const int s = r * JW + warp;
+                const int s = r * RW + warp;
                 if (s >= b || C.rid[s] < 0) continue;
                 const float a = ar[r];
                 if (a <= C.floor2 || bq <= C.floor2) {
@@ -541,46 +477,54 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
 #pragma unroll
                         for (int u = 0; u < kRegL; ++u) x[r][u] = 0.0f;
                         ar[r] = 0.0f;
+                        dx[r] = 1.0f;
                     }
                     if (bq <= C.floor2 && bq != 0.0f) {
 #pragma unroll
                         for (int u = 0; u < kRegL; ++u) y[u] = 0.0f;
                         bq = 0.0f;
+                        dy = 1.0f;
                         ymod = true;
                     }
                     continue;
                 }
-                float g0 = 0.0f, g1 = 0.0f;
+                float g0 = 0.0f, g1 = 0.0f, g2 = 0.0f, g3 = 0.0f;
 #pragma unroll
-                for (int u = 0; u < kRegL; u += 2) {
+                for (int u = 0; u < kRegL; u += 4) {
                     g0 = fmaf(x[r][u], y[u], g0);
                     g1 = fmaf(x[r][u + 1], y[u + 1], g1);
+                    g2 = fmaf(x[r][u + 2], y[u + 2], g2);
+                    g3 = fmaf(x[r][u + 3], y[u + 3], g3);
                 }
-                const float g = warp_sum(g0 + g1);
+                const float g = warp_sum((g0 + g1) + (g2 + g3)) * (dx[r] * dy);
                 if (g == 0.0f || fabsf(g) <= C.tol * sqrtf(a) * sqrtf(bq)) continue;
                 float cs, sn, tt;
-                rot_params(a, bq, g, cs, sn, tt);
+                rot_params_fast(a, bq, g, cs, sn, tt);
                 if (tt == 0.0f) continue;
                 if (lane == 0) atomicMax(C.rho2, __float_as_uint(g / a * (g / bq)));
+                const float ratio = __fdividef(dy, dx[r]);
+                const float al = tt * ratio, be = __fdividef(tt, ratio);
 #pragma unroll
                 for (int u = 0; u < kRegL; ++u) {
                     const float xv = x[r][u], yv = y[u];
-                    x[r][u] = fmaf(cs, xv, -sn * yv);
-                    y[u] = fmaf(sn, xv, cs * yv);
+                    x[r][u] = fmaf(-al, yv, xv);
+                    y[u] = fmaf(be, xv, yv);
                 }
                 rotate_m(C, s, b + q, cs, sn, lane);
+                dx[r] *= cs;
+                dy *= cs;
                 float na = fmaf(-tt, g, a), nq = fmaf(tt, g, bq);
                 if (na < 0.1f * a) {
                     float s0 = 0.0f;
 #pragma unroll
                     for (int u = 0; u < kRegL; ++u) s0 = fmaf(x[r][u], x[r][u], s0);
-                    na = warp_sum(s0);
+                    na = warp_sum(s0) * (dx[r] * dx[r]);
                 }
                 if (nq < 0.1f * bq) {
                     float s0 = 0.0f;
 #pragma unroll
                     for (int u = 0; u < kRegL; ++u) s0 = fmaf(y[u], y[u], s0);
-                    nq = warp_sum(s0);
+                    nq = warp_sum(s0) * (dy * dy);
                 }
                 ar[r] = na;
                 bq = nq;
@@ -594,58 +538,81 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
                     if (e < L) rq[e] = y[u];
                 }
                 __syncwarp();
-                if (lane == 0) C.nrm[b + q] = bq;
+                if (lane == 0) {
+                    C.nrm[b + q] = bq;
+                    C.dsc[q] = dy;
+                }
             }
         }
         __syncthreads();
     }
-    // store: block 0 from registers, block 1 from shared memory
+    // store: block 0 from registers, block 1 from shared memory, scales multiplied in
 #pragma unroll
     for (int r = 0; r < kRegRows; ++r) {
-        const int s = r * JW + warp;
+        const int s = r * RW + warp;
         if (s >= b || C.rid[s] < 0) continue;
         float* w = W + (size_t)C.rid[s] * ld;
 #pragma unroll
         for (int u = 0; u < kRegL; ++u) {
             const int e = u * 32 + lane;
-            if (e < L) __stcg(w + e, x[r][u]);
+            if (e < L) __stcg(w + e, x[r][u] * dx[r]);
         }
         if (lane == 0) __stcg(snorm + C.rid[s], (double)ar[r]);
     }
-    for (int s = warp; s < b; s += JW) {
+    for (int s = warp; s < b; s += RW) {
         const int row = C.rid[b + s];
         if (row < 0) continue;
         const float* src = C.rows + (size_t)s * L;
+        const float dv = C.dsc[s];
         float* w = W + (size_t)row * ld;
-        for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
+        for (int k = lane; k < L; k += 32) __stcg(w + k, src[k] * dv);
         if (lane == 0) __stcg(snorm + row, (double)C.nrm[b + s]);
     }
     if (lane == 0 && rot > 0) atomicOr(&s_any, 1);
     __syncthreads();
-    // U32 rows <- M U32 rows, one column per thread (M's rows and columns past
-    // 2b are unit vectors; z is 0 there)
+    // U32 rows <- M U32 rows in column tiles of kZT staged in shared memory (the
+    // W rows are stored, so their space is free): thread (rg, cg) of 16 x 32
+    // computes rows 4 rg .. 4 rg + 3 and columns 4 cg .. 4 cg + 3 of the tile,
+    // reading M^T and the tile as float4
     if (s_any) {
-        for (int k = threadIdx.x; k < c; k += JT) {
-            float z[kM];
-#pragma unroll
-            for (int j = 0; j < kM; ++j) {
-                const int row = j < 2 * b ? C.rid[j] : -1;
-                z[j] = row >= 0 ? __ldcg(Z + (size_t)row * ld + k) : 0.0f;
+        float* Zt = C.rows;              // [kM][kZT]
+        float* Mt = C.rows + kM * kZT;   // [kM][kM]: M transposed
+        for (int i = threadIdx.x; i < kM * kM; i += RT) Mt[(i % kM) * kM + i / kM] = C.M[i];
+        const int rg = threadIdx.x >> 5, cg = threadIdx.x & 31;
+        const int n2 = 2 * b;
+        for (int k0 = 0; k0 < c; k0 += kZT) {
+            __syncthreads();
+            for (int e = threadIdx.x; e < kM * (kZT / 4); e += RT) {
+                const int j = e / (kZT / 4), kk = 4 * (e % (kZT / 4));
+                const int row = j < n2 ? C.rid[j] : -1;
+                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (row >= 0 && k0 + kk < c) v = __ldcg(reinterpret_cast<const float4*>(Z + (size_t)row * ld + k0 + kk));
+                *reinterpret_cast<float4*>(Zt + j * kZT + kk) = v;
             }
-            for (int i = 0; i < 2 * b; ++i) {
-                const int row = C.rid[i];
-                if (row < 0) continue;
-                const float4* m4 = reinterpret_cast<const float4*>(C.M + i * kM);
-                float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            __syncthreads();
+            float acc[4][4];
 #pragma unroll
-                for (int j4 = 0; j4 < kM / 4; ++j4) {
-                    const float4 m = m4[j4];
-                    s0 = fmaf(m.x, z[4 * j4], s0);
-                    s1 = fmaf(m.y, z[4 * j4 + 1], s1);
-                    s2 = fmaf(m.z, z[4 * j4 + 2], s2);
-                    s3 = fmaf(m.w, z[4 * j4 + 3], s3);
-                }
-                __stcg(Z + (size_t)row * ld + k, (s0 + s1) + (s2 + s3));
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = 0.0f;
+#pragma unroll 4
+            for (int j = 0; j < n2; ++j) {
+                const float4 m = *reinterpret_cast<const float4*>(Mt + j * kM + 4 * rg);
+                const float4 z = *reinterpret_cast<const float4*>(Zt + j * kZT + 4 * cg);
+                const float mv[4] = {m.x, m.y, m.z, m.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = fmaf(mv[ii], zv[kk], acc[ii][kk]);
+            }
+            const int k = k0 + 4 * cg;
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                const int i = 4 * rg + ii;
+                const int row = i < n2 ? C.rid[i] : -1;
+                if (row >= 0 && k < c)
+                    __stcg(reinterpret_cast<float4*>(Z + (size_t)row * ld + k),
+                           make_float4(acc[ii][0], acc[ii][1], acc[ii][2], acc[ii][3]));
             }
         }
     }
@@ -654,7 +621,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
 }
 
 template <typename T>
-__global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
+__global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
                                                        double tol_in, unsigned long long timeout_ns, int ld) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -710,7 +677,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
 
     // squared row norms of the FP64 input (for the zero floor and the FP32 scale)
     const double* W64 = kF32 ? d.W0 : d.W;
-    for (int row = g * JW + warp; row < c; row += G * JW) {
+    for (int row = g * kWarps<T> + warp; row < c; row += G * kWarps<T>) {
         const double* w = W64 + (size_t)row * ld;
         double a = 0.0;
         for (int i = lane; i < L; i += 32) {
@@ -735,7 +702,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
     }
     __syncthreads();
     // initial Z (identity, or Zinit) and, for the FP32 pass, the scaled copy of the rows
-    for (int row = g * JW + warp; row < c; row += G * JW) {
+    for (int row = g * kWarps<T> + warp; row < c; row += G * kWarps<T>) {
         if (Z) {
             bool copied = false;
             if constexpr (!kF32) {
@@ -760,7 +727,8 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
         RC.rows = reinterpret_cast<float*>(smem_raw);
         RC.M = reinterpret_cast<float*>(smem_raw + (size_t)kJacobiRegL * kMaxB * 4);
         RC.nrm = RC.M + kM * kM;
-        RC.rid = reinterpret_cast<int*>(RC.nrm + kM);
+        RC.dsc = RC.nrm + kM;
+        RC.rid = reinterpret_cast<int*>(RC.dsc + kM / 2);
         RC.rho2 = &s_rho2;
         RC.b = b;
         RC.L = L;
@@ -776,7 +744,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
             int rot = 0;
             if (threadIdx.x == 0) s_rho2 = 0u;
             // fresh squared row norms, then the tail threshold (same in every CTA)
-            for (int row = g * JW + warp; row < c; row += G * JW) {
+            for (int row = g * kWarps<T> + warp; row < c; row += G * kWarps<T>) {
                 const T* w = W + (size_t)row * ld;
                 T a = 0;
                 for (int i = lane; i < L; i += 32) {
@@ -802,7 +770,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                         }
                     }
                     // load the two blocks (slot s < b: block bl[0]; s >= b: block bl[1])
-                    for (int s = warp; s < 2 * b; s += JW) {
+                    for (int s = warp; s < 2 * b; s += kWarps<T>) {
                         const int blk = bl[s / b];
                         const int row = blk * b + (s % b);
                         const bool ok = blk < nb && row < c;
@@ -828,7 +796,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
                     __syncthreads();
                     rot += process_block_pair(C, b, r == 0, warp, lane);
                     // store back
-                    for (int s = warp; s < 2 * b; s += JW) {
+                    for (int s = warp; s < 2 * b; s += kWarps<T>) {
                         const int row = C.rid[s];
                         if (row < 0) continue;
                         const T* src = C.rows + (size_t)s * C.rowlen;
@@ -865,7 +833,7 @@ __global__ void __launch_bounds__(JT, 1) jacobi_kernel(const OpDesc* descs, cons
             used = sweep + 1;
         }
         if constexpr (!kF32) {   // rows out of their scales (the last round ended with a barrier)
-            for (int row = g * JW + warp; row < c; row += G * JW) {
+            for (int row = g * kWarps<T> + warp; row < c; row += G * kWarps<T>) {
                 const double dv = __ldcg(dscale + row);
                 if (dv == 1.0) continue;
                 T* w = W + (size_t)row * ld;
@@ -890,7 +858,6 @@ timeout:
 
 }  // namespace
 
-int jacobi_threads() { return JT; }
 size_t jacobi_sync_words_per_op() { return kSyncWords; }
 
 
@@ -906,9 +873,9 @@ cudaError_t jacobi_max_resident(int* blocks) {
     if ((e = cudaFuncSetAttribute(jacobi_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemF32)) !=
         cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, jacobi_kernel<double>, JT, kSmemBytes)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per64, jacobi_kernel<double>, kThreads<double>, kSmemBytes)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, jacobi_kernel<float>, JT, kSmemF32)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, jacobi_kernel<float>, kThreads<float>, kSmemF32)) != cudaSuccess)
         return e;
     *blocks = sms * (per64 < per32 ? per64 : per32);
     return cudaSuccess;
@@ -922,7 +889,8 @@ cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, c
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
                     (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
     const void* fn = fp32 ? (const void*)jacobi_kernel<float> : (const void*)jacobi_kernel<double>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(JT), args, fp32 ? kSmemF32 : kSmemBytes, st);
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(fp32 ? kThreads<float> : kThreads<double>), args,
+                                       fp32 ? kSmemF32 : kSmemBytes, st);
 }
 
 }  // namespace mpdo
