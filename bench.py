@@ -318,6 +318,13 @@ def run_arm(args, precision, world, dist, local):
             "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
+# chain20_chi256 mixed workload) moved by one chunk of ops through the SVD kernels:
+# FP32 and FP64 Jacobi, two FP64 and one FP32 preconditioner GEMM launches.  To be
+# re-measured whenever one of those kernels changes.
+SVD_DRAM_BYTES_PER_CHUNK = 395.5e6
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -451,7 +458,10 @@ def main():
         "roofline": {"kernel": "truncation SVD (jacobi_svd%s)" % (" + jacobi_fp32 + precond_gemm" if hp == "mixed"
                                                                     else ""),
                      "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None, "traffic": None,
+                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
+                     "traffic": (SVD_DRAM_BYTES_PER_CHUNK if (args.workload == "chain20_chi256" and hp == "mixed")
+                                 else None),
+                     "traffic_unit": "bytes per chunk of ops (one launch of each SVD kernel)",
                      "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
                              "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
                              "MEASURED_PEAKS.json)"},
