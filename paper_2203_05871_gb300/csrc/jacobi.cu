@@ -306,7 +306,7 @@ static_assert(RT == (kM / 4) * (kZT / 4), "one 4 x 4 output tile per thread");
 static_assert(kM * kZT + kM * kM <= kJacobiRegL * kMaxB, "U32 tile and M^T fit the rows' space");
 
 struct RegCtx {
-    float* rows;      // [b][L]: the W rows of the block in shared memory
+    float* rows;      // [b][kJacobiRegL]: the W rows of the block in shared memory, zero past L
     float* M;         // [kM][kM]: accumulated rotation of the block pair's rows (row-major)
     float* nrm;       // [2b]: squared norms (slot s of block k at k b + s)
     float* dsc;       // [b]: scales of block 1's rows during the cross pairs
@@ -343,8 +343,8 @@ __device__ __forceinline__ void rotate_m(const RegCtx& C, int ip, int iq, float 
 __device__ int intra_pair_reg(const RegCtx& C, int p, int q, int mo, int lane) {
     const int ip = mo + p, iq = mo + q;
     if (C.rid[ip] < 0 || C.rid[iq] < 0) return 0;
-    float* rp = C.rows + (size_t)p * C.L;
-    float* rq = C.rows + (size_t)q * C.L;
+    float* rp = C.rows + (size_t)p * kJacobiRegL;
+    float* rq = C.rows + (size_t)q * kJacobiRegL;
     const float a = C.nrm[ip], b = C.nrm[iq];
     if (a <= C.floor2 || b <= C.floor2) {
         if (a <= C.floor2 && a != 0.0f) {
@@ -401,14 +401,19 @@ __device__ int intra_block_reg(const RegCtx& C, int mo, int warp, int lane) {
     return rot;
 }
 
-// W rows of accumulator slots s0 .. s0 + b - 1 into the shared-memory rows
+// W rows of accumulator slots s0 .. s0 + b - 1 into the shared-memory rows,
+// zero-padded to kJacobiRegL (the padding stays zero under every rotation, so
+// the register loops need no bound on the row length)
 __device__ __forceinline__ void load_block_reg(const RegCtx& C, const float* W, int ld, int s0, int warp, int lane) {
     for (int s = warp; s < C.b; s += RW) {
         const int row = C.rid[s0 + s];
-        if (row < 0) continue;
+        float* dst = C.rows + (size_t)s * kJacobiRegL;
+        if (row < 0) {
+            for (int k = lane; k < kJacobiRegL; k += 32) dst[k] = 0.0f;
+            continue;
+        }
         const float* w = W + (size_t)row * ld;
-        float* dst = C.rows + (size_t)s * C.L;
-        for (int k = lane; k < C.L; k += 32) dst[k] = __ldcg(w + k);
+        for (int k = lane; k < kJacobiRegL; k += 32) dst[k] = k < C.L ? __ldcg(w + k) : 0.0f;
     }
 }
 
@@ -444,10 +449,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
         ar[r] = own ? C.nrm[s] : 0.0f;
         dx[r] = 1.0f;
 #pragma unroll
-        for (int u = 0; u < kRegL; ++u) {
-            const int e = u * 32 + lane;
-            x[r][u] = (own && e < L) ? C.rows[(size_t)s * L + e] : 0.0f;
-        }
+        for (int u = 0; u < kRegL; ++u) x[r][u] = own ? C.rows[(size_t)s * kJacobiRegL + u * 32 + lane] : 0.0f;
     }
     __syncthreads();
     // block 1 into shared memory
@@ -458,13 +460,10 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     for (int t = 0; t < b; ++t) {
         const int q = (t + warp) % b;
         if (warp < b && C.rid[b + q] >= 0) {
-            float* rq = C.rows + (size_t)q * L;
+            float* rq = C.rows + (size_t)q * kJacobiRegL;
             float y[kRegL];
 #pragma unroll
-            for (int u = 0; u < kRegL; ++u) {
-                const int e = u * 32 + lane;
-                y[u] = e < L ? rq[e] : 0.0f;
-            }
+            for (int u = 0; u < kRegL; ++u) y[u] = rq[u * 32 + lane];
             float bq = C.nrm[b + q], dy = C.dsc[q];
             bool ymod = false;
 #pragma unroll
@@ -533,10 +532,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
             }
             if (ymod) {
 #pragma unroll
-                for (int u = 0; u < kRegL; ++u) {
-                    const int e = u * 32 + lane;
-                    if (e < L) rq[e] = y[u];
-                }
+                for (int u = 0; u < kRegL; ++u) rq[u * 32 + lane] = y[u];
                 __syncwarp();
                 if (lane == 0) {
                     C.nrm[b + q] = bq;
@@ -562,7 +558,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     for (int s = warp; s < b; s += RW) {
         const int row = C.rid[b + s];
         if (row < 0) continue;
-        const float* src = C.rows + (size_t)s * L;
+        const float* src = C.rows + (size_t)s * kJacobiRegL;
         const float dv = C.dsc[s];
         float* w = W + (size_t)row * ld;
         for (int k = lane; k < L; k += 32) __stcg(w + k, src[k] * dv);
