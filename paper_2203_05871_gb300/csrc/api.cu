@@ -250,6 +250,7 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.jb32 = tuned_block_rows(c, d.cl, d.cr, true, jacobi_block_rows_f32(d.L, d.c));
     d.sweeps_out = c->d_sweeps + s;
     d.forced_k = 0;
+    d.full_svd = c->full_svd ? 1 : 0;
     d.tape_V = nullptr;
     d.tape_s = nullptr;
     d.W0 = c->mixed ? c->d_W0 + (size_t)s * mat : d.W;
@@ -274,6 +275,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
             fk = c->forced[((size_t)d.b * c->forced_steps + step) * c->n_ops + d.op];
         d.forced_k = fk;
         d.tape_V = tape ? tape[s].V : nullptr;
+        if (tape) d.full_svd = 1;
         d.tape_s = tape ? tape[s].s : nullptr;
         work[s] = (double)d.c * d.c * (double)d.L;
         qwork[s] = (double)d.m * d.n * d.c;

@@ -62,6 +62,7 @@ struct mpdo_ctx {
     int dev = 0;
     int N = 0, B = 0, cap = 0, ld = 0;
     bool built = false;
+    bool full_svd = false;   // set while the gradient runs: every SVD keeps all its singular vectors
     // schedule
     std::vector<mpdo::Layer> layers;
     std::vector<double> weights;

@@ -416,12 +416,23 @@ int plan_tape(mpdo_ctx* c, GradState* g, int s, std::vector<std::vector<TapeRec>
 
 extern "C" {
 
+namespace {
+// the gradient's forward and backward keep every singular vector (the SVD
+// backward uses the complete V), so no Jacobi pair is skipped meanwhile
+struct FullSvdScope {
+    mpdo_ctx* c;
+    explicit FullSvdScope(mpdo_ctx* x) : c(x) { c->full_svd = true; }
+    ~FullSvdScope() { c->full_svd = false; }
+};
+}  // namespace
+
 int mpdo_grad_forward(mpdo_ctx* c, int n_steps) {
     if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
     CU(cudaSetDevice(c->dev));
     if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
     if (n_steps < 1) return fail(MPDO_EINVAL, "n_steps must be >= 1");
     if (sites_f32(c)) return fail(MPDO_EINVAL, "the gradient needs MPDO_STORE_F64 site storage");
+    FullSvdScope full(c);
     if (!c->grad) {
         c->grad = new (std::nothrow) GradState();
         if (!c->grad) return fail(MPDO_ENOMEM, "host allocation failed");
@@ -469,6 +480,7 @@ int mpdo_grad_backward(mpdo_ctx* c, const double* zbar, const double* wbar, doub
     GradState* g = c->grad;
     if (!g || !g->recorded) return fail(MPDO_ESTATE, "mpdo_grad_forward must come first");
     if (g->gen != c->gen) return fail(MPDO_ESTATE, "the state changed since mpdo_grad_forward");
+    FullSvdScope full(c);
     const int B = c->B, N = c->N, cap = c->cap, P = 6 * N + 2 * c->nb;
     int rc = alloc_backward(c, g);
     if (rc) return rc;

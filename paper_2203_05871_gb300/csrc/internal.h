@@ -72,6 +72,7 @@ struct OpDesc {
     int* rank_log;     // &log[b][step*n_ops + op] or nullptr
     int* sweeps_out;   // Jacobi sweeps used (or nullptr)
     int forced_k;      // > 0: truncation rank imposed (replay of a recorded run)
+    int full_svd;      // 1: orthogonalise every pair of rows (the adjoint needs all singular vectors)
     double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr
     double* tape_s;    // adjoint recompute: all c sorted singular values
 };

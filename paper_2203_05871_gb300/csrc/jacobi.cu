@@ -88,6 +88,7 @@ struct Ctx {
     unsigned* rho2;   // largest g^2 / (a b) rotated in this CTA and sweep (float bits)
     int rowlen, L;    // row length in smem (W part + Z part), W part length
     T floor2, tol;
+    double thr;       // FP64 pass: pairs of rows whose squared norms are both below thr are skipped
 };
 
 // Rotation parameters (cs, sn, t) zeroing <w_p, w_q> = g for |w_p|^2 = a,
@@ -185,6 +186,9 @@ __device__ int scaled_rotate(const Ctx<T>& C, int p, int q, T* rp, T* rq, double
 template <typename T>
 __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
     if (C.rid[p] < 0 || C.rid[q] < 0) return 0;
+    if constexpr (sizeof(T) == 8) {
+        if (C.nrm[p] < C.thr && C.nrm[q] < C.thr) return 0;   // two rows the truncation discards
+    }
     T* rp = C.rows + (size_t)p * C.rowlen;
     T* rq = C.rows + (size_t)q * C.rowlen;
     const T a = C.nrm[p], b = C.nrm[q];
@@ -616,6 +620,36 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     return rot;
 }
 
+// The kk-th largest of v[0..c) (non-negative), by bisection on the bit
+// pattern (non-negative doubles order like their bits).  Called by every
+// thread of a CTA of kThreads<double>; every thread returns the same value.
+constexpr int kSelPer = (4 * kMaxChi + kThreads<double> - 1) / kThreads<double>;
+__device__ double kth_largest(const double* v, int c, int kk) {
+    __shared__ int s_cnt[kWarps<double>];
+    unsigned long long key[kSelPer];
+#pragma unroll
+    for (int i = 0; i < kSelPer; ++i) {
+        const int j = threadIdx.x + i * kThreads<double>;
+        key[i] = j < c ? (unsigned long long)__double_as_longlong(fmax(__ldcg(v + j), 0.0)) : 0ull;
+    }
+    unsigned long long x = 0ull;
+    for (int bit = 62; bit >= 0; --bit) {
+        const unsigned long long cand = x | (1ull << bit);
+        int n = 0;
+#pragma unroll
+        for (int i = 0; i < kSelPer; ++i) n += key[i] >= cand;
+        n = __reduce_add_sync(0xffffffffu, n);
+        if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = n;
+        __syncthreads();
+        int tot = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps<double>; ++w) tot += s_cnt[w];
+        __syncthreads();
+        if (tot >= kk) x = cand;
+    }
+    return __longlong_as_double((long long)x);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
@@ -665,6 +699,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
     C.rid = reinterpret_cast<int*>(C.dsc + 2 * b);
     double* dscale = d.snorm + ld;   // FP64 pass: per-row scales (the QR's column norms are dead here)
     C.rho2 = &s_rho2;
+    C.thr = 0.0;
     {
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
         const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
@@ -755,6 +790,23 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                 if (lane == 0) __stcg(d.snorm + row, (double)a);
             }
             if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
+            if constexpr (!kF32) {
+                // Rows the truncation discards (below the chi_max + max(16, chi_max / 8)
+                // largest) must end orthogonal to the kept rows, not to one another:
+                // the kept rows are then exact singular vectors, the discarded weight
+                // is the sum of the discarded rows' squared norms (a trace), and
+                // rows already orthogonal to ~1e-4 have norms equal to their singular
+                // values to ~1e-8, far finer than the margin.  So once the previous
+                // sweep rotated by at most 1e-4, pairs of two discarded rows are skipped.
+                if (threadIdx.x == 0) {
+                    const int kk = d.chi_max + max(16, d.chi_max / 8);
+                    s_conv = sweep > 0 && !d.full_svd && kk < c &&
+                             __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep - 1])) <= 1e-8f;
+                }
+                __syncthreads();
+                C.thr = s_conv ? kth_largest(d.snorm, c, d.chi_max + max(16, d.chi_max / 8)) : 0.0;
+                __syncthreads();
+            }
             for (int r = 0; r < nbp - 1; ++r) {
                 for (int i = g; i < npair; i += G) {
                     const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
@@ -764,6 +816,15 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                             rot += block_pair_reg(RC, W, Z, ld, c, nb, bl, r == 0, d.snorm, warp, lane);
                             continue;
                         }
+                    }
+                    if constexpr (!kF32) {   // both blocks discarded: nothing to do
+                        int pred = 1;
+                        if (threadIdx.x < 2 * b) {
+                            const int blk = bl[threadIdx.x / b];
+                            const int row = blk * b + (threadIdx.x % b);
+                            if (blk < nb && row < c) pred = __ldcg(d.snorm + row) < C.thr;
+                        }
+                        if (__syncthreads_and(pred)) continue;
                     }
                     // load the two blocks (slot s < b: block bl[0]; s >= b: block bl[1])
                     for (int s = warp; s < 2 * b; s += kWarps<T>) {
