@@ -62,7 +62,7 @@ void free_all(mpdo_ctx* c) {
 
 int release_slots(mpdo_ctx* c) {
     void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps,
-                    c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm, c->d_copy};
+                    c->d_pre_ok, c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm, c->d_copy};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
@@ -78,6 +78,7 @@ int release_slots(mpdo_ctx* c) {
     c->d_cta = nullptr;
     c->d_sync = nullptr;
     c->d_sweeps = nullptr;
+    c->d_pre_ok = nullptr;
     if (c->h_desc) cudaFreeHost(c->h_desc);
     if (c->h_cta) cudaFreeHost(c->h_cta);
     c->h_desc = nullptr;
@@ -109,6 +110,7 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_Yk, (size_t)s * c->cap * c->ld));
     CU(dalloc(&c->d_snorm, (size_t)s * 2 * c->ld));
     CU(dalloc(&c->d_sweeps, (size_t)s));
+    CU(dalloc(&c->d_pre_ok, (size_t)s));
     c->h_sweeps.assign(s, 0);
     CU(dalloc(&c->d_desc, (size_t)s));
     const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), s);
@@ -249,6 +251,7 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.jb = tuned_block_rows(c, d.cl, d.cr, false, jacobi_block_rows(d.L, d.c, 8));
     d.jb32 = tuned_block_rows(c, d.cl, d.cr, true, jacobi_block_rows_f32(d.L, d.c));
     d.sweeps_out = c->d_sweeps + s;
+    d.pre_ok = c->mixed ? c->d_pre_ok + s : nullptr;
     d.forced_k = 0;
     d.full_svd = c->full_svd ? 1 : 0;
     d.tape_V = nullptr;

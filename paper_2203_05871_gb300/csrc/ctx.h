@@ -85,6 +85,7 @@ struct mpdo_ctx {
     int slots = 0;
     double *d_thetap = nullptr, *d_W = nullptr, *d_Z = nullptr, *d_Yk = nullptr, *d_snorm = nullptr;
     int* d_sweeps = nullptr;      // [slots] Jacobi sweeps of the last chunk
+    int* d_pre_ok = nullptr;      // [slots] mixed path: the FP32 pass ended by its off-orthogonality rule
     bool mixed = false;           // mixed-precision SVD (FP32 preconditioning + FP64 finish)
     double *d_W0 = nullptr, *d_E = nullptr, *d_Q = nullptr;
     float *d_W32 = nullptr, *d_U32 = nullptr;

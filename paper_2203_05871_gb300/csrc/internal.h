@@ -71,6 +71,9 @@ struct OpDesc {
     double* max_disc;  // per-instance max discarded weight
     int* rank_log;     // &log[b][step*n_ops + op] or nullptr
     int* sweeps_out;   // Jacobi sweeps used (or nullptr)
+    int* pre_ok;       // mixed path: 1 when the FP32 pass ended with every pair orthogonal to ~1e-6
+                       // (its last sweep rotated by at most 1e-3); written by that pass, read by
+                       // the FP64 pass (or nullptr)
     int forced_k;      // > 0: truncation rank imposed (replay of a recorded run)
     int full_svd;      // 1: orthogonalise every pair of rows (the adjoint needs all singular vectors)
     double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr

@@ -706,6 +706,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
         C.tol = (T)tol;
     }
 
+    if (kF32 && g == 0 && threadIdx.x == 0 && d.pre_ok) *d.pre_ok = 0;   // set again only on success
     // squared row norms of the FP64 input (for the zero floor and the FP32 scale)
     const double* W64 = kF32 ? d.W0 : d.W;
     for (int row = g * kWarps<T> + warp; row < c; row += G * kWarps<T>) {
@@ -798,13 +799,20 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                 // rows already orthogonal to ~1e-4 have norms equal to their singular
                 // values to ~1e-8, far finer than the margin.  So once the previous
                 // sweep rotated by at most 1e-4, pairs of two discarded rows are skipped.
+                // The first sweep after the FP32 preconditioner qualifies too when that
+                // pass ended by its off-orthogonality rule (every pair at ~1e-6 then).
                 if (threadIdx.x == 0) {
                     const int kk = d.chi_max + max(16, d.chi_max / 8);
-                    s_conv = sweep > 0 && !d.full_svd && kk < c &&
-                             __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep - 1])) <= 1e-8f;
+                    const bool settled = sweep > 0
+                                             ? __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep - 1])) <= 1e-8f
+                                             : (d.pre_ok && __ldcg(d.pre_ok) == 1);
+                    s_conv = settled && !d.full_svd && kk < c;
                 }
                 __syncthreads();
-                C.thr = s_conv ? kth_largest(d.snorm, c, d.chi_max + max(16, d.chi_max / 8)) : 0.0;
+                // the threshold is fixed when the gate first opens, so that a row
+                // near it keeps its side (a row changing side later would bring its
+                // unprocessed pairs back and cost another sweep)
+                if (s_conv && C.thr == 0.0) C.thr = kth_largest(d.snorm, c, d.chi_max + max(16, d.chi_max / 8));
                 __syncthreads();
             }
             for (int r = 0; r < nbp - 1; ++r) {
@@ -903,8 +911,10 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
             if (!kF32) {
                 if (d.sweeps_out) *d.sweeps_out += used;
                 if (!conv) atomicOr(d.status, (int)MPDO_ST_NOCONV);
-            } else if (d.sweeps_out) {
-                *d.sweeps_out += used << 16;   // FP32 sweeps in the high half
+            } else {
+                if (d.sweeps_out) *d.sweeps_out += used << 16;   // FP32 sweeps in the high half
+                if (d.pre_ok)
+                    *d.pre_ok = used > 0 && __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + used - 1])) <= 1e-6f;
             }
         }
     }

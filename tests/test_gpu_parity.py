@@ -192,6 +192,10 @@ def test_chi256_one_step_sampled():
     pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
     g = s.measure_2q(pairs, "ZZ", connected=True)[0]
     assert np.abs(g - o.zz_connected(pairs)).max() <= TOL
+    # the largest relative discarded weight of the step (a sum over the
+    # discarded rows, whose mutual orthogonality the SVD does not need)
+    md = s.status()["max_discarded"][0]
+    assert o.max_discarded > 0.0 and abs(md - o.max_discarded) <= 1e-9 * o.max_discarded
 
 
 # ---------------------------------------------------------------------------
@@ -250,6 +254,8 @@ def test_mixed_chi256_one_step_sampled(decay, tol):
     g, rg = s.measure_2q(pairs, "ZZ", connected=True)[0], o.zz_connected(pairs)
     scale = np.array([abs(o.state.expect_2q(i, j)) + abs(rz[i] * rz[j]) for (i, j) in pairs])
     assert np.all(np.abs(g - rg) <= tol * np.maximum(1.0, scale))
+    md = s.status()["max_discarded"][0]
+    assert o.max_discarded > 0.0 and abs(md - o.max_discarded) <= tol * o.max_discarded
 
 
 def test_mixed_long_rows_chi300():
