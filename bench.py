@@ -322,7 +322,7 @@ def run_arm(args, precision, world, dist, local):
 # chain20_chi256 mixed workload) moved by one chunk of ops through the SVD kernels:
 # FP32 and FP64 Jacobi, two FP64 and one FP32 preconditioner GEMM launches.  To be
 # re-measured whenever one of those kernels changes.
-SVD_DRAM_BYTES_PER_CHUNK = 395.5e6
+SVD_DRAM_BYTES_PER_CHUNK = 385.6e6
 
 
 def measured_peaks():
@@ -462,9 +462,11 @@ def main():
                      "traffic": (SVD_DRAM_BYTES_PER_CHUNK if (args.workload == "chain20_chi256" and hp == "mixed")
                                  else None),
                      "traffic_unit": "bytes per chunk of ops (one launch of each SVD kernel)",
-                     "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)); peak = nominal "
-                             "FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; no measured FP64 peak in "
-                             "MEASURED_PEAKS.json)"},
+                     "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)), the FP64 work of "
+                             "an ideal Golub-Kahan SVD; peak = nominal FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x "
+                             "2.07 GHz; no measured FP64 peak in MEASURED_PEAKS.json). The mixed path does most of "
+                             "the orthogonalisation in FP32 and skips the pairs of rows the truncation discards, "
+                             "so frac can exceed 1"},
         "roofline_contraction": contraction_roofline(prof) if hp == "mixed" else None,
         "autotune": {"jacobi_rows_per_block": head["tuned"],
                      "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},
