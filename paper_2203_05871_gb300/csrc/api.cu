@@ -344,7 +344,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
         CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
         CU(launch_jacobi(c->d_desc, nops, dbase, dbase + total, dbase + 2 * total, c->d_sync, total,
-                         fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : c->cfg.jacobi_tol,
+                         fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : fp64_jacobi_tol(c),
                          timeout_ns, ld, fp32, c->st));
         return MPDO_OK;
     };

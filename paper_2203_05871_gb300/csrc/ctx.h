@@ -185,6 +185,16 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d);
 // truncate, reconstruct.  forced (per item, or nullptr) imposes ranks; tape
 // (per item, or nullptr) records what the adjoint needs; log_ranks writes the
 // ranks into c->rank_log at row `step`.
+// Orthogonality tolerance of the FP64 Jacobi pass.  The mixed path's
+// contractions carry ~1e-7 relative error (TF32 split), so its FP64 finish
+// stops at 1e-10 (singular values stay exact to ~1e-20, vectors to ~1e-10,
+// five orders inside the mixed path's 1e-5 bound) instead of sqrt(L) eps;
+// the FP64 path, an explicit jacobi_tol and the gradient keep the strict one.
+constexpr double kMixedFinishTol = 1e-10;
+inline double fp64_jacobi_tol(const mpdo_ctx* c) {
+    return (c->cfg.jacobi_tol <= 0.0 && c->mixed && !c->full_svd) ? kMixedFinishTol : c->cfg.jacobi_tol;
+}
+
 int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,
               bool log_ranks);
 

@@ -196,7 +196,7 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
             }
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
             CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync, g->Rj,
-                             c->cfg.jacobi_max_sweeps, c->cfg.jacobi_tol, timeout_ns, ld, false, st));
+                             c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
             CU(launch_truncate(ch.d_desc, nops, cap, st));
             if (c->mixed)
                 CU(launch_tc_reconstruct(ch.d_desc, nops, cap, st));

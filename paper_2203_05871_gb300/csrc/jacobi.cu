@@ -700,10 +700,12 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
     double* dscale = d.snorm + ld;   // FP64 pass: per-row scales (the QR's column norms are dead here)
     C.rho2 = &s_rho2;
     C.thr = 0.0;
+    float rho2_stop;
     {
         const double eps = kF32 ? (double)FLT_EPSILON : DBL_EPSILON;
         const double tol = tol_in > 0.0 ? tol_in : sqrt((double)(L > 1 ? L : 1)) * eps;
         C.tol = (T)tol;
+        rho2_stop = (float)(1e-6 * tol);
     }
 
     if (kF32 && g == 0 && threadIdx.x == 0 && d.pre_ok) *d.pre_ok = 0;   // set again only on success
@@ -888,11 +890,12 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
             // when the largest relative off-orthogonality rotated away was at most
             // 1e-3: the rows are then orthogonal to ~1e-6, FP32's rounding level
             // for these inner products, and further sweeps only chase rounding.
-            // FP64: no rotation, or the largest rotated was below 1e-10: the next
-            // sweep would meet pairs at ~1e-20, far under tol, and rotate nothing
+            // FP64: no rotation, or the largest rotated rho had rho^2 <= 1e-6 tol: by
+            // quadratic convergence the next sweep would meet pairs at ~rho^2, far
+            // under tol, and rotate nothing (1e-20 for tol = sqrt(L) eps at L = 1024)
             if (threadIdx.x == 0)
                 s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u)) ||
-                         (__uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= (kF32 ? 1e-6f : 1e-20f));
+                         (__uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= (kF32 ? 1e-6f : rho2_stop));
             __syncthreads();
             conv = s_conv;
             used = sweep + 1;

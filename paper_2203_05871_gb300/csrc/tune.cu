@@ -56,7 +56,7 @@ int time_jacobi(mpdo_ctx* c, std::vector<OpDesc>& h, bool fp32, int b, double* m
     CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
     CU(cudaEventRecord(e0, c->st));
     CU(launch_jacobi(c->d_desc, nops, c->d_cta, c->d_cta + total, c->d_cta + 2 * total, c->d_sync, total,
-                     fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : c->cfg.jacobi_tol, timeout_ns, ld,
+                     fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : fp64_jacobi_tol(c), timeout_ns, ld,
                      fp32, c->st));
     CU(cudaEventRecord(e1, c->st));
     CU(cudaEventSynchronize(e1));
