@@ -410,7 +410,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
             const OpDesc& d = c->h_desc[s];
             maxc = std::max(maxc, d.c);
             maxL = std::max(maxL, d.L);
-            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0};
+            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0, 1};
             g2[s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0, 0};
             g3[s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0, 0};
             fl_gemm += 2.0 * d.c * d.c * d.c * 2 + 2.0 * d.c * d.c * d.L;

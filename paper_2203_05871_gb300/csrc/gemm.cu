@@ -7,6 +7,10 @@
 // written as double.  One launch serves a list of problems of different
 // sizes (grid.z = problem); CTAs outside a problem's tiles return at once.
 // 64 x 64 tiles, k-step 16, 256 threads with a 4 x 4 register tile each.
+// A symmetric product (sym: E = U U^T) computes the tiles on and above the
+// diagonal only and writes each strictly upper tile to both triangles; entry
+// (j, i) is then the same products summed in the same order as (i, j), so
+// the result is bitwise that of the full product.
 #include "internal.h"
 
 namespace mpdo {
@@ -26,6 +30,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* descs) {
     const GemmDesc& g = descs[blockIdx.z];
     const int i0 = blockIdx.y * GT, j0 = blockIdx.x * GT;
     if (i0 >= g.M || j0 >= g.N) return;
+    if (g.sym && i0 > j0) return;   // the mirror of a tile above the diagonal
     __shared__ TC As[GK][GT + 1];
     __shared__ TC Bs[GK][GT + 1];
     const int t = threadIdx.x, ty = t >> 4, tx = t & 15;
@@ -89,6 +94,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(const GemmDesc* descs) {
             if (g.D) r += g.beta * load_as<double>(g.D, g.d_f32, (size_t)gi * g.ldd + gj);
             if (g.sub_identity && gi == gj) r -= 1.0;
             g.C[(size_t)gi * g.ldc + gj] = r;
+            if (g.sym && i0 < j0) g.C[(size_t)gj * g.ldc + gi] = r;
         }
     }
 }

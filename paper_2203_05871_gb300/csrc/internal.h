@@ -182,6 +182,8 @@ struct GemmDesc {
     int ldd, d_f32;
     int sub_identity;
     int a_trans;      // A stored K x M (default 0)
+    int sym;          // 1: C is symmetric (A B with B = A^T, D = nullptr): only the tiles on and
+                      // above the diagonal are computed, each written to both triangles
 };
 cudaError_t launch_gemm(const GemmDesc* d_desc, int count, int max_m, int max_n, bool fp32_compute,
                         cudaStream_t st);
