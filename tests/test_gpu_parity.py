@@ -323,6 +323,27 @@ def test_errors_are_codes_not_crashes():
     s.step(1)
 
 
+def test_profile_counters():
+    """Kernel timers and sweep counters (mpdo_profile_*): every kernel of the
+    mixed step is timed, the SVDs' mean and critical-path sweeps are
+    consistent, and a reset zeroes them."""
+    wl = W.chain8_fp64()
+    s = solver_for(wl, precision=_mixed())
+    s.profile(True)
+    s.step(3)
+    p = s.profile_read(reset=True)
+    for k in ["merge_gate", "qr", "jacobi_fp32", "precond_gemm", "jacobi_svd", "truncate", "reconstruct"]:
+        assert p[k]["launches"] > 0 and p[k]["ms"] > 0.0, k
+    j = p["jacobi_svd"]
+    assert j["svds"] == 3 * s.op_counts()[0]
+    assert j["chunks"] > 0
+    # per chunk the slowest op needs at least one sweep and at most all the chunk's sweeps
+    assert j["chunks"] <= j["critical_sweeps"] <= j["sweeps"]
+    assert j["chunks"] <= j["critical_sweeps_fp32"] <= j["sweeps_fp32"]
+    q = s.profile_read()
+    assert q["jacobi_svd"]["svds"] == 0 and q["jacobi_svd"]["chunks"] == 0 and q["qr"]["launches"] == 0
+
+
 # ---------------------------------------------------------------------------
 # the step captured as a CUDA graph
 # ---------------------------------------------------------------------------
