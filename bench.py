@@ -348,6 +348,16 @@ def contraction_roofline(prof):
                     "x 1.1/2.25 (nominal TF32/BF16)" + ("" if bf16 else "; of fallback")}
 
 
+def qr_roofline(prof):
+    """Householder QR with column pivoting against the nominal FP64 peak."""
+    q = prof["qr"]
+    achieved = q["flops"] / (q["ms"] / 1e3) / 1e12 if q["ms"] > 0 else None
+    return {"kernel": "qr_kernel (Householder, column pivoting)", "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_NOMINAL_TFLOPS if achieved else None, "traffic": None,
+            "note": "flops 4 m n r - 2 (m + n) r^2 + 4/3 r^3 per op (r = min(m, n)); peak = nominal FP64"}
+
+
 def run_adjoint(args, local):
     """One gradient (checkpointed forward + backward) of sum_i zbar_i <z_i> +
     sum_{i<j} wbar_ij conn_ij on the N=24 ring (closing bond routed by swaps)
@@ -468,6 +478,7 @@ def main():
                              "the orthogonalisation in FP32 and skips the pairs of rows the truncation discards, "
                              "so frac can exceed 1"},
         "roofline_contraction": contraction_roofline(prof) if hp == "mixed" else None,
+        "roofline_qr": qr_roofline(prof),
         "autotune": {"jacobi_rows_per_block": head["tuned"],
                      "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},
         "graph_step": {"ms_per_step": head["graph_ms"] / args.steps,
