@@ -35,6 +35,17 @@
 // A row whose norm is at most eps * ||W||_F (FP64 eps, in both passes) is
 // numerically zero: it is set to zero and never rotated (its direction is
 // rounding noise).
+//
+// Further pieces, each described where it is implemented:
+//  - FP32 pass on rows of at most 1024 elements: the register path (16 warps,
+//    one block of each pair in registers, U32 turned by the block pair's
+//    accumulated rotation);
+//  - FP64 pass: scaled (fast) rotations, one FMA per element (scaled_rotate);
+//  - FP64 pass: pairs of two rows the truncation discards are skipped once the
+//    ranking is settled (kth_largest and the sweep-start gate);
+//  - convergence: the FP32 pass stops at <= c/4 rotations or a largest rotated
+//    off-orthogonality of 1e-3, the FP64 pass at no rotation or a largest
+//    rotated rho with rho^2 <= 1e-6 tol.
 #include <float.h>
 #include <mpdo.h>
 
