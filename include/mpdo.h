@@ -193,6 +193,18 @@ int mpdo_gates(mpdo_ctx *ctx, int b, double *out, long long cap);
 int mpdo_schedule(int n, int n_bonds, const int *bond_i, const int *bond_j, int *ops, long long cap,
                   int *n_ops);
 
+/* Host-side fault injection, for testing the failure handling (Sec. 2.5's
+ * solver has none; every device-side wait here is bounded).  kind =
+ * MPDO_FAULT_DROP_CTA: the next Householder QR launch of mpdo_trotter_step
+ * leaves out one CTA of the first op that was planned two or more, while that
+ * op's group still counts it; the op's other CTAs then wait at their first
+ * barrier for a CTA that never arrives, give up after cfg.barrier_timeout_ms,
+ * record MPDO_ST_TIMEOUT for the op's instance and return, and the step
+ * returns MPDO_ETIMEOUT.  The GPU context stays usable.  One-shot (cleared once
+ * applied); kind = 0 cancels.  EINVAL for an unknown kind. */
+enum { MPDO_FAULT_DROP_CTA = 1 };
+int mpdo_inject_fault(mpdo_ctx *ctx, int kind);
+
 /* Kernel timing.  mpdo_profile_enable(ctx, 1) brackets every kernel launch
  * of the step with CUDA events on the context stream and accumulates, per
  * kernel kind k (0 merge+gate, 1 Jacobi SVD (FP64), 2 truncate, 3 reconstruct,
@@ -217,25 +229,31 @@ int mpdo_profile_sweeps(mpdo_ctx *ctx, long long *sweeps, long long *svds, long 
 int mpdo_profile_sweeps_critical(mpdo_ctx *ctx, long long *crit, long long *crit_fp32, long long *chunks);
 
 /* mpdo_measure_1q without any device allocation, on a state held in the
- * caller's device memory.  For callers that cannot call cudaMalloc: code that
- * runs while a stream is being captured into a CUDA graph, or frameworks that
- * give all device memory to their own allocator up front.  The paper has no
- * counterpart; it is the same computation as mpdo_measure_1q.
+ * caller's device memory.  For callers that cannot call cudaMalloc: frameworks
+ * that give all device memory to their own allocator up front (a hidden
+ * allocation would fail or break their accounting), and code whose rules
+ * forbid the runtime's allocator.  The paper has no counterpart; it is the
+ * same computation as mpdo_measure_1q.
  *   sites   device, [batch][n_qubits][chi_cap][4][chi_cap] doubles, the site
- *           tensors (l, a, r) of each instance (the layout libmpdo keeps)
+ *           tensors (l, a, r) of each instance (f64 elements only, the layout
+ *           of an MPDO_STORE_F64 context)
  *   dims    device, [batch][n_qubits+1] ints, bond dimensions, dims[0] =
  *           dims[n_qubits] = 1, each in [1, chi_cap]
  *   qubits  device, [nq] ints in [0, n_qubits)
  *   out     device, [batch][nq] doubles: <sigma^comp_q> / tr rho
  *   cuda_stream  cudaStream_t the work is ordered on (NULL = default stream)
+ * dims and qubits are read on the device, so the host cannot check them: the
+ * call clamps them into range before any kernel uses them, and writes NaN to
+ * out[b][k] when a bond dimension of instance b or qubits[k] was out of range.
  * Scratch: a static device array of 2^18 doubles (2 MiB) that every device
- * loading the library keeps until the process exits; sizes with
- * 2 * batch * (n_qubits + 1) * chi_cap > 2^18 are rejected with ECAPACITY.
+ * loading the library keeps until the process exits; a call needs
+ * 2 * batch * (n_qubits + 1) * chi_cap doubles plus batch * (n_qubits + 2) +
+ * 2 * nq ints (two per double), and larger sizes are rejected with ECAPACITY.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current): make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents;
- * calls that overlap on the GPU race on it.  Asynchronous: returns after
- * queuing the kernels; EINVAL / ECAPACITY / ECUDA with mpdo_last_error(). */
+ * device, with that device current).  All calls share the array and it keeps
+ * the last call's contents; calls that overlap on the GPU race on it.
+ * Asynchronous: returns after queuing the kernels; EINVAL / ECAPACITY / ECUDA
+ * with mpdo_last_error(). */
 int mpdo_measure_1q_noalloc(const double *sites, const int *dims, int n_qubits, int batch, int chi_cap,
                             const int *qubits, int nq, char comp, double *out, void *cuda_stream);
 

@@ -372,14 +372,25 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         }
         int* hbase = c->h_cta + (size_t)2 * (2 * gcap + c->slots);
         int* dbase = c->d_cta + (size_t)2 * (2 * gcap + c->slots);
+        // fault injection (host side): leave out the last CTA of the first op that
+        // has two or more, while its group still counts it, so that the op's first
+        // barrier cannot complete and its CTAs give up after barrier_timeout_ms
+        int drop_op = -1;
+        if (c->inject == MPDO_FAULT_DROP_CTA)
+            for (int s = 0; s < nops && drop_op < 0; ++s)
+                if (G[s] >= 2) drop_op = s;
+        const int launched = total - (drop_op >= 0 ? 1 : 0);
         int t = 0;
         for (int s = 0; s < nops; ++s) {
-            hbase[2 * total + s] = G[s];
-            for (int g = 0; g < G[s]; ++g, ++t) {
+            hbase[2 * launched + s] = G[s];
+            const int run = G[s] - (s == drop_op ? 1 : 0);
+            for (int g = 0; g < run; ++g, ++t) {
                 hbase[t] = s;
-                hbase[total + t] = g;
+                hbase[launched + t] = g;
             }
         }
+        if (drop_op >= 0) c->inject = 0;
+        total = launched;
         double fl_qr = 0.0;
         for (int s = 0; s < nops; ++s) {
             const OpDesc& d = c->h_desc[s];
@@ -569,8 +580,10 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     if (cfg->n_qubits < 3) return fail(MPDO_EINVAL, "n_qubits must be >= 3");
     if (cfg->batch < 1) return fail(MPDO_EINVAL, "batch must be >= 1");
     if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
-    if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32 && cfg->precision != MPDO_MIXED_BF16X3)
-        return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
+    if (cfg->precision == MPDO_MIXED_BF16X3)
+        return fail(MPDO_EINVAL, "MPDO_MIXED_BF16X3 is not built yet");
+    if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32)
+        return fail(MPDO_EINVAL, "precision must be MPDO_FP64 or MPDO_MIXED_TF32");
     if (cfg->storage != MPDO_STORE_F64 && cfg->storage != MPDO_STORE_F32)
         return fail(MPDO_EINVAL, "storage must be MPDO_STORE_F64 or MPDO_STORE_F32");
     if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
@@ -991,6 +1004,13 @@ int mpdo_schedule(int n, int n_bonds, const int* bond_i, const int* bond_j, int*
             ++k;
         }
     *n_ops = (int)k;
+    return MPDO_OK;
+}
+
+int mpdo_inject_fault(mpdo_ctx* c, int kind) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    if (kind != 0 && kind != MPDO_FAULT_DROP_CTA) return fail(MPDO_EINVAL, "unknown fault kind");
+    c->inject = kind;
     return MPDO_OK;
 }
 

@@ -19,6 +19,7 @@ MPDO_OK, MPDO_EINVAL, MPDO_ENOMEM, MPDO_ECUDA, MPDO_ENOCONV, MPDO_ETIMEOUT, MPDO
     MPDO_ECAPACITY, MPDO_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7, -8
 ST_NOCONV, ST_NONFINITE, ST_TIMEOUT, ST_CAPACITY = 1, 2, 4, 8
 FP64, MIXED_TF32, MIXED_BF16X3 = 0, 1, 2
+FAULT_DROP_CTA = 1
 STORE_F64, STORE_F32 = 0, 1
 
 _ERR_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOCONV", -5: "ETIMEOUT",
@@ -88,6 +89,7 @@ def load_library(path: str = LIB_PATH):
         "mpdo_measure_1q_noalloc": (ctypes.c_int, [vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp,
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
+        "mpdo_inject_fault": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_autotune": (ctypes.c_int, [vp, _ip, ctypes.c_int, _ip]),
         "mpdo_grad_forward": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_grad_backward": (ctypes.c_int, [vp, _dp, _dp, _dp, _dp]),
@@ -109,7 +111,7 @@ def exported_symbols() -> list[str]:
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
-            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_grad_forward",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -338,6 +340,11 @@ class Solver:
         r = _as(ranks, np.int32).reshape(self.batch, -1)
         assert r.shape[1] % n_ops == 0
         _check(self._lib.mpdo_force_ranks(self._h, _ptr(r, ctypes.c_int), r.shape[1] // n_ops))
+
+    def inject_fault(self, kind: int = FAULT_DROP_CTA):
+        """Host-side fault injection (mpdo_inject_fault): the next QR launch
+        leaves out one CTA of an op, whose barrier then times out."""
+        _check(self._lib.mpdo_inject_fault(self._h, int(kind)))
 
     # -- adjoint ----------------------------------------------------------
     def n_params(self):
