@@ -140,3 +140,19 @@ class DenseTrotter:
         c[i] = 3
         c[j] = 3
         return pauli_expect(self.r.reshape(-1), self.n, c)
+
+
+def renyi2(rho):
+    """Sec. 2.3 Eq. (S_2) on the dense matrix: S2 = -ln tr(rho^2) of rho / tr rho."""
+    t = np.trace(rho).real
+    return float(-np.log(np.trace(rho @ rho).real / (t * t)))
+
+
+def osee(r, n, bond):
+    """Sec. 2.3 Eq. (OSEE) from the dense coefficient vector r (4^n entries):
+    singular values of r reshaped to (4^(bond+1), 4^(n-bond-1)) by LAPACK,
+    then the entropy of their normalised squares."""
+    s = np.linalg.svd(np.asarray(r).real.reshape(4 ** (bond + 1), -1), compute_uv=False)
+    p = s * s / np.sum(s * s)
+    p = p[p > 0.0]
+    return float(-np.sum(p * np.log(p)))

@@ -102,6 +102,49 @@ class MPOState:
         self.B[0] = self.B[0] / t
         return t
 
+    def norm2(self):
+        """<<rho|rho>> = sum_a r_a^2, the squared norm of the coefficient MPS:
+        E_{p+1} = sum_s B_p[s]^T E_p B_p[s], E_0 = [[1]]."""
+        E = np.ones((1, 1))
+        for b in self.B:
+            E = sum(b[:, s, :].T @ E @ b[:, s, :] for s in range(4))
+        return float(E[0, 0])
+
+    def renyi2(self):
+        """Second Renyi entropy, Sec. 2.3 Eq. (S_2): S2 = -ln tr(rho^2) of the
+        normalised rho.  The basis P_a/sqrt2 is orthonormal for the trace
+        inner product, so tr(rho^2) = sum_a r_a^2 = norm2(), and normalising
+        rho divides it by (tr rho)^2."""
+        t = self.trace()
+        return -np.log(self.norm2() / (t * t))
+
+    def schmidt_values(self, bond):
+        """Schmidt values of |rho>> for the cut between path positions bond
+        and bond+1: canonicalise both sides with QR (numpy), then the SVD of
+        the product of the two triangular factors."""
+        R = np.ones((1, 1))
+        for p in range(bond + 1):
+            M = np.einsum("ij,jsr->isr", R, self.B[p])
+            M = M.reshape(-1, M.shape[2])
+            _, R = np.linalg.qr(M)
+        Lf = np.ones((1, 1))
+        for p in range(self.n - 1, bond, -1):
+            M = np.einsum("lsr,rj->lsj", self.B[p], Lf)
+            M = M.reshape(M.shape[0], -1)
+            _, Rt = np.linalg.qr(M.T)
+            Lf = Rt.T
+        return np.linalg.svd(R @ Lf, compute_uv=False)
+
+    def osee(self, bond):
+        """Operator space entanglement entropy, Sec. 2.3 Eq. (OSEE): the von
+        Neumann entropy of the normalised vectorised state |rho>> for the cut
+        after path position bond, -sum_k p_k ln p_k with p_k = s_k^2 / sum s^2
+        from the Schmidt values s_k."""
+        s = self.schmidt_values(bond)
+        p = s * s / np.sum(s * s)
+        p = p[p > 0.0]
+        return float(-np.sum(p * np.log(p)))
+
     def expect_1q(self, i, comp="Z"):
         c = [0] * self.n
         c[i] = PAULI_INDEX[comp]
