@@ -6,18 +6,26 @@ couplings of the precision-comparison model (J_b~U[0.05,0.15],
 Omega~U[0.3,0.7], g0_i~U[0.005,0.02], g2_i~U[0.01,0.03], h_z alternating 0,1),
 chi_max = 256 saturated from the first step (seeded random MPO start), cutoff
 1e-10, dt = 0.02, second-order Trotter: 29 two-site gate applications per step,
-18 of them on 1024 x 1024 bond matrices.
+most of them on bond matrices of up to 1024 x 1024.
 
 A step = one mpdo_trotter_step(1) over the whole batch (merge, gate, weight,
-Jacobi SVD, truncation, reconstruction for every op, trace forcing).
-``value`` = gate applications per second (device-timed, inputs resident),
-``e2e`` = same through the C ABI with the state uploaded from host memory and
-observables read back each step.
+QR + Jacobi SVD, truncation, reconstruction for every op, trace forcing).
+``value`` = gate applications per second of the batched mixed-precision path
+(device-timed, inputs resident); ``fp64_path`` = the same steps on the FP64
+path, ``fp64_per_gate`` = the FP64 path with one op in flight at a time (the
+plain per-gate path), ``speedup_mixed_vs_fp64`` = their ratio to ``value``;
+``batched`` = the 64-instance N=16 workload; ``e2e`` = the headline metric
+through the C ABI with the state uploaded from host memory and observables
+read back each step.
 
 --gpus N > 1 runs N independent replicas (one per rank, launched by torchrun):
 the method has no exchange step between instances.
-``--impl reference`` times the CPU oracle (plain C Jacobi, one thread) on a
-bounded sample: each step is one 1024 x 1024 gate application.
+``--impl reference`` times the CPU oracle on the machine's host cores: each step is
+one gate application of the workload (ops taken in step order, cycling), with
+the oracle's LAPACK SVD route (numpy, all host cores), the paper's own
+threaded-LAPACK design.  ``cpu_baseline`` (in the GPU line) times the same
+route on 5 ops after one warm-up op, and ``cpu_baseline_plain`` one op of the
+oracle's plain C Jacobi on one thread.
 ``--probe-peaks`` measures the FP64 / FP32 / TF32 GEMM rates with cuBLAS.
 ``adjoint`` (``--adjoint-steps``, default 1): one gradient of the observables
 on the N=24 ring at chi = 256 (checkpointed forward, then recompute and
@@ -45,8 +53,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain20_chi256")
-    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--per-gate-steps", type=int, default=1,
+                    help="timed steps of the FP64 path with one op in flight (0: skip)")
+    ap.add_argument("--batched-steps", type=int, default=1,
+                    help="timed steps of the 64-instance batched workload (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-ops", type=int, default=5, help="timed oracle ops of cpu_baseline")
+    ap.add_argument("--no-cpu-plain", action="store_true", help="skip the plain C Jacobi op")
+    ap.add_argument("--oracle-svd", default="lapack", choices=["lapack", "jacobi"],
+                    help="SVD route of --impl reference")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--probe-peaks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default Jacobi block rule")
@@ -137,35 +153,56 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-def oracle_sample(wl, dims, tens, reps, warm):
-    """Time the oracle on full-size (1024 x 1024) gate applications, one
-    thread.  Returns (seconds per op, description)."""
+def cpu_info():
+    """Host CPU model and core count (recorded next to every CPU number)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
+def oracle_ops(wl, dims, tens, count, warm, svd_impl):
+    """Time the oracle's two-site update on the workload's ops in step order
+    (cycling), each from the saturated start state.  Returns (per-op seconds of
+    the timed ops, description)."""
     import numpy as np
     from oracle import schedule, tebd
     layers = schedule.step_layers(wl.n, wl.bonds)
     gates = tebd.build_gates(wl, 0, layers, wl.dt)
+    ops = [(op[1], G) for L, gl in zip(layers, gates) for op, G in zip(L, gl)]
     st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
     cap = int(wl.chi_max[0])
-    # the first op of the step whose bond matrix is (4 cap) x (4 cap)
-    pick = None
-    for L, gl in zip(layers, gates):
-        for op, G in zip(L, gl):
-            p = op[1]
-            if dims[p] == cap and dims[p + 2] == cap:
-                pick = (p, G)
-                break
-        if pick:
-            break
-    p, G = pick
-    times = []
-    for r in range(warm + reps):
+    times, sizes = [], []
+    for r in range(warm + count):
+        p, G = ops[r % len(ops)]
         s = st.copy()
         t0 = time.perf_counter()
-        s.apply(p, G, cap, float(wl.cutoff[0]))
+        s.apply(p, G, cap, float(wl.cutoff[0]), svd_impl=svd_impl)
         dt = time.perf_counter() - t0
         if r >= warm:
             times.append(dt)
-    return times, f"gate application on a {4 * cap}x{4 * cap} bond matrix (op at p={p}), plain C Jacobi"
+            sizes.append(f"{4 * dims[p]}x{4 * dims[p + 2]}")
+    route = ("oracle MPO-TEBD update, LAPACK gesdd SVD through numpy (threaded BLAS)" if svd_impl == "lapack"
+             else "oracle MPO-TEBD update, plain C one-sided Jacobi SVD, one thread")
+    return times, f"{len(times)} ops of the step in order after {warm} warm-up (bond matrices {', '.join(sizes)}); {route}"
 
 
 def run_reference(args):
@@ -175,36 +212,38 @@ def run_reference(args):
     wl, states, cap = make_workload(args.workload)
     b = next(i for i in range(wl.batch) if int(wl.chi_max[i]) == cap)   # an instance at full chi
     dims, tens = states[b]
-    times, what = oracle_sample(wl.instance(b), dims, tens, args.steps, min(args.warmup, 1))
+    threads = os.cpu_count() if args.oracle_svd == "lapack" else 1
+    times, what = oracle_ops(wl.instance(b), dims, tens, args.steps, args.warmup, args.oracle_svd)
     v = len(times) / sum(times)
+    info = cpu_info()
     line = {"impl": "reference", "metric": "gate_applications_per_sec", "value": v,
-            "unit": "gate-applications/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": min(args.warmup, 1),
+            "unit": "gate-applications/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "oracle": "CPU FP64, one thread"},
-            "cpu_baseline": {"value": v, "unit": "gate-applications/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} x {what}"},
+            "config": {"workload": args.workload, "oracle": what, "step": "one gate application"},
+            "cpu_baseline": {"value": v, "unit": "gate-applications/s", "cores": threads, "kind": "oracle",
+                             "sample": what, "cpu": info},
             "e2e": {"value": v, "unit": "gate-applications/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
-def cpu_baseline_subprocess(args):
-    """Run the oracle sample in a child process with one BLAS thread."""
+def cpu_baseline_subprocess(args, svd_impl, count, warm):
+    """The oracle sample in a child process: LAPACK route on every host core,
+    or the plain C Jacobi route with one BLAS thread."""
     env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
+    if svd_impl == "jacobi":
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
     env.pop("RANK", None)
     env.pop("WORLD_SIZE", None)
-    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", "1", "--warmup", "0",
-           "--workload", args.workload]
+    cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--steps", str(count), "--warmup",
+           str(warm), "--workload", args.workload, "--oracle-svd", svd_impl]
     try:
-        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=600).stdout
+        out = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900).stdout
         line = json.loads(out.strip().splitlines()[-1])
-        cb = line["cpu_baseline"]
-        cb["sample"] += " (1 op; no warm-up)"
-        return cb
+        return line["cpu_baseline"]
     except Exception as ex:  # baseline failure must not hide the GPU number
-        return {"value": None, "unit": "gate-applications/s", "cores": 1, "kind": "oracle",
+        return {"value": None, "unit": "gate-applications/s", "cores": None, "kind": "oracle",
                 "sample": f"failed: {ex}"}
 
 
@@ -240,19 +279,24 @@ def probe_peaks():
 
 
 # ---------------------------------------------------------------------------
-def run_arm(args, precision, world, dist, local):
-    """Time args.steps Trotter steps of one precision; returns a result dict."""
+def run_arm(args, precision, world, dist, local, workload=None, steps=None, warmup=None, max_slots=0,
+            graph=True, e2e_steps=None, autotune=True):
+    """Time Trotter steps of one precision on one workload; returns a result dict."""
     import numpy as np
     import torch
     from paper_2203_05871_gb300 import FP64, MIXED_TF32, Solver
 
-    wl, states, cap = make_workload(args.workload)
+    workload = workload or args.workload
+    steps = args.steps if steps is None else steps
+    warmup = args.warmup if warmup is None else warmup
+    e2e_steps = args.e2e_steps if e2e_steps is None else e2e_steps
+    wl, states, cap = make_workload(workload)
     stream = torch.cuda.Stream()
     s = Solver(wl.n, batch=wl.batch, chi_cap=cap, stream=stream,
-               precision=FP64 if precision == "fp64" else MIXED_TF32)
+               precision=FP64 if precision == "fp64" else MIXED_TF32, max_slots=max_slots)
     s.build_gates(wl)
     tuned = None
-    if not args.no_autotune:
+    if autotune and not args.no_autotune:
         from paper_2203_05871_gb300.mpdo import saturated_classes
         cls = saturated_classes(wl.n, cap)
         tuned = {f"{a}x{b}": [int(x) for x in blk] for (a, b), blk in zip(cls, s.autotune(cls))}
@@ -260,15 +304,16 @@ def run_arm(args, precision, world, dist, local):
         s.set_state(b, dims, tens)
     n_ops, n_swaps, _ = s.op_counts()
     n_ops_all = n_ops * wl.batch
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         s.step(1)
     torch.cuda.synchronize()
+    chi_warm = s.status()["chi"]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     s.profile(True)
     s.profile_read(reset=True)
     ms = 0.0
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1.0)                       # L2 flush between timed steps
             torch.cuda.synchronize()
             if dist:
@@ -282,19 +327,21 @@ def run_arm(args, precision, world, dist, local):
             ms += e0.elapsed_time(e1)
     prof = s.profile_read(reset=True)
     s.profile(False)
-    # the same steps replayed as a captured CUDA graph (first call captures)
-    s.step(1, graph=True)
-    graph_ms = 0.0
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+    graph_ms = None
+    if graph:
+        # the same steps replayed as a captured CUDA graph (first call captures)
         s.step(1, graph=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        graph_ms += e0.elapsed_time(e1)
+        graph_ms = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(1, graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            graph_ms += e0.elapsed_time(e1)
     if dist:
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -303,7 +350,7 @@ def run_arm(args, precision, world, dist, local):
     # end to end through the C ABI from host buffers (state in, observables out)
     flat_bytes = sum(int(np.asarray(t).size) for (_, tens) in states for t in tens) * 8
     e2e_ms = 0.0
-    for _ in range(args.e2e_steps):
+    for _ in range(e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for b, (dims, tens) in enumerate(states):
@@ -312,17 +359,9 @@ def run_arm(args, precision, world, dist, local):
         s.measure_1q(range(wl.n), "Z")
         e2e_ms += (time.perf_counter() - t0) * 1e3
     s.close()
-    return {"wl": wl, "cap": cap, "n_ops": n_ops_all, "n_swaps": n_swaps, "ms": ms, "graph_ms": graph_ms,
-            "prof": prof,
-            "status": st, "tuned": tuned,
-            "clocks": clk.summary(), "e2e_ms": e2e_ms, "flat_bytes": flat_bytes}
-
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
-# chain20_chi256 mixed workload) moved by one chunk of ops through the SVD kernels:
-# FP32 and FP64 Jacobi, two FP64 and one FP32 preconditioner GEMM launches.  To be
-# re-measured whenever one of those kernels changes.
-SVD_DRAM_BYTES_PER_CHUNK = 395.7e6
+    return {"wl": wl, "cap": cap, "n_ops": n_ops_all, "n_swaps": n_swaps, "ms": ms, "steps": steps,
+            "graph_ms": graph_ms, "prof": prof, "status": st, "tuned": tuned, "chi_warm": chi_warm,
+            "clocks": clk.summary(), "e2e_ms": e2e_ms, "e2e_steps": e2e_steps, "flat_bytes": flat_bytes}
 
 
 def measured_peaks():
@@ -410,6 +449,43 @@ def run_adjoint(args, local):
             "loss": float(L[0]), "chi_max_seen": int(st["chi"].max()), "clocks": clk.summary()}
 
 
+KERNELS_PER_PROFILED_LAUNCH = {"precond_gemm": 3}   # the three preconditioner GEMMs share one timer
+
+
+def arm_summary(r, world):
+    """Throughput and kernel split of one timed arm."""
+    prof = r["prof"]
+    jac = prof["jacobi_svd"]
+    steps = r["steps"]
+    out = {"value": world * r["n_ops"] * steps / (r["ms"] / 1e3), "ms_per_step": r["ms"] / steps,
+           "kernels": {k: {"ms_per_step": v["ms"] / steps, "launches_per_step": v["launches"] / steps}
+                       for k, v in prof.items() if v["launches"]},
+           "jacobi_mean_sweeps": (jac["sweeps"] / jac["svds"] if jac["svds"] else None),
+           "jacobi_mean_sweeps_fp32": (jac["sweeps_fp32"] / jac["svds"] if jac["svds"] else None),
+           "svd_n_effective": ((jac["flops"] / 21.0 / jac["svds"]) ** (1.0 / 3.0) if jac["svds"] else None),
+           "chi_after_warmup": [int(x) for x in r["chi_warm"][0]], "clocks": r["clocks"]}
+    return out
+
+
+def truncation_roofline(prof, precision):
+    """The truncation stage (QR + SVD, about 95% of the step) against the FP64
+    peak, with the fixed algorithmic convention of 21 n^3 flops per n x n SVD."""
+    jac = prof["jacobi_svd"]
+    parts = ["qr", "jacobi_svd"] + (["jacobi_fp32", "precond_gemm"] if precision == "mixed" else [])
+    ms = sum(prof[k]["ms"] for k in parts)
+    achieved = jac["flops"] / (ms / 1e3) / 1e12 if ms > 0 else None
+    names = {"qr": "qr_kernel", "jacobi_svd": "jacobi_kernel<double>", "jacobi_fp32": "jacobi_kernel<float>",
+             "precond_gemm": "gemm_kernel x3"}
+    return {"kernel": "truncation stage: " + " + ".join(names[k] for k in parts),
+            "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+            "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
+            "traffic": None,
+            "note": "achieved = 21 n^3 flops per n x n SVD (n = 4 max(chi_l, chi_r)), the FP64 work of an ideal "
+                    "Golub-Kahan SVD, over the summed CUDA-event time of the listed kernels (QR included); peak = "
+                    "nominal FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; MEASURED_PEAKS.json has no "
+                    "FP64 figure), of nominal; traffic: not re-captured for these kernels"}
+
+
 def main():
     args = parse()
     if args.probe_peaks:
@@ -432,23 +508,22 @@ def main():
     if dist:
         dist.barrier()
     arms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    res = {p: run_arm(args, p, world, dist, local) for p in arms}
+    res = {p: run_arm(args, p, world, dist, local, graph=(p == arms[-1]),
+                      e2e_steps=(args.e2e_steps if p == arms[-1] else 0)) for p in arms}
     head = res["mixed"] if "mixed" in res else res["fp64"]
     hp = "mixed" if "mixed" in res else "fp64"
     wl, cap, n_ops = head["wl"], head["cap"], head["n_ops"]
-    ms_per_step = head["ms"] / args.steps
-    value = world * n_ops * args.steps / (head["ms"] / 1e3)
+    hs = arm_summary(head, world)
     e2e_value = world * n_ops * args.e2e_steps / (head["e2e_ms"] / 1e3) if args.e2e_steps > 0 else None
     prof = head["prof"]
-    jac = prof["jacobi_svd"]
-    svd_ms = jac["ms"] + prof["jacobi_fp32"]["ms"] + prof["precond_gemm"]["ms"]
-    achieved = jac["flops"] / (svd_ms / 1e3) / 1e12 if svd_ms > 0 else None
-    launches = sum(v["launches"] for v in prof.values())
+    launches = sum(v["launches"] * KERNELS_PER_PROFILED_LAUNCH.get(k, 1) for k, v in prof.items())
+    dtype = ("mixed: tcgen05 tf32x3 contractions (fp64 re-accumulated), fp32-preconditioned fp64 QR + Jacobi SVD"
+             if hp == "mixed" else "f64")
     line = {
-        "metric": "gate_applications_per_sec", "value": value, "unit": "gate-applications/s",
-        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "s_per_trotter_step": ms_per_step / 1e3,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "metric": "gate_applications_per_sec", "value": hs["value"], "unit": "gate-applications/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": hs["ms_per_step"],
+        "s_per_trotter_step": hs["ms_per_step"] / 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
         "data": "synthetic",
         "config": {"workload": args.workload, "n_qubits": wl.n, "batch": wl.batch, "chi_max": cap,
                    "cutoff": float(wl.cutoff[0]),
@@ -459,45 +534,54 @@ def main():
         "e2e": {"value": e2e_value, "unit": "gate-applications/s", "h2d_bytes_per_step": head["flat_bytes"],
                 "d2h_bytes_per_step": wl.n * wl.batch * 8},
         "gpu_launches": launches,
-        "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] / args.steps}
-                    for k, v in prof.items() if v["launches"]},
-        "jacobi_mean_sweeps": (jac["sweeps"] / jac["svds"] if jac["svds"] else None),
-        "jacobi_mean_sweeps_fp32": (jac["sweeps_fp32"] / jac["svds"] if jac["svds"] else None),
-        "jacobi_critical_sweeps": ([jac["critical_sweeps"] / jac["chunks"], jac["critical_sweeps_fp32"] / jac["chunks"]]
-                                   if jac.get("chunks") else None),
-        "roofline": {"kernel": "truncation SVD (jacobi_svd%s)" % (" + jacobi_fp32 + precond_gemm" if hp == "mixed"
-                                                                    else ""),
-                     "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                     "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
-                     "traffic": (SVD_DRAM_BYTES_PER_CHUNK if (args.workload == "chain20_chi256" and hp == "mixed")
-                                 else None),
-                     "traffic_unit": "bytes per chunk of ops (one launch of each SVD kernel)",
-                     "note": "algorithmic flops 21 n^3 per n x n SVD (n = 4 max(chi_l, chi_r)), the FP64 work of "
-                             "an ideal Golub-Kahan SVD; peak = nominal FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x "
-                             "2.07 GHz; no measured FP64 peak in MEASURED_PEAKS.json). The mixed path does most of "
-                             "the orthogonalisation in FP32 and skips the pairs of rows the truncation discards, "
-                             "so frac can exceed 1"},
+        "kernels": hs["kernels"],
+        "jacobi_mean_sweeps": hs["jacobi_mean_sweeps"],
+        "jacobi_mean_sweeps_fp32": hs["jacobi_mean_sweeps_fp32"],
+        "svd_n_effective": hs["svd_n_effective"],
+        "chi_after_warmup": hs["chi_after_warmup"],
+        "jacobi_critical_sweeps": ([prof["jacobi_svd"]["critical_sweeps"] / prof["jacobi_svd"]["chunks"],
+                                    prof["jacobi_svd"]["critical_sweeps_fp32"] / prof["jacobi_svd"]["chunks"]]
+                                   if prof["jacobi_svd"].get("chunks") else None),
+        "roofline": truncation_roofline(prof, hp),
         "roofline_contraction": contraction_roofline(prof) if hp == "mixed" else None,
         "roofline_qr": qr_roofline(prof),
         "autotune": {"jacobi_rows_per_block": head["tuned"],
                      "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},
-        "graph_step": {"ms_per_step": head["graph_ms"] / args.steps,
-                       "note": "same steps replayed from one captured CUDA graph (device-side planning)"},
+        "graph_step": ({"ms_per_step": head["graph_ms"] / args.steps,
+                        "note": "same steps replayed from one captured CUDA graph (device-side planning)"}
+                       if head["graph_ms"] is not None else None),
         "clocks": head["clocks"],
         "status": int(head["status"]["status"][0]), "chi_max_seen": int(head["status"]["chi"].max()),
     }
     if "fp64" in res and hp != "fp64":
-        f = res["fp64"]
-        line["fp64_path"] = {"value": world * f["n_ops"] * args.steps / (f["ms"] / 1e3),
-                             "ms_per_step": f["ms"] / args.steps,
-                             "jacobi_mean_sweeps": (f["prof"]["jacobi_svd"]["sweeps"] / f["prof"]["jacobi_svd"]["svds"]
-                                                    if f["prof"]["jacobi_svd"]["svds"] else None),
-                             "clocks": f["clocks"]}
-        line["speedup_mixed_vs_fp64"] = f["ms"] / head["ms"]
+        f = arm_summary(res["fp64"], world)
+        f["dtype"] = "f64"
+        f["note"] = "the same workload, steps and start on the FP64 path (FP64 contractions, FP64 QR + Jacobi)"
+        line["fp64_path"] = f
+        line["speedup_mixed_vs_fp64"] = res["fp64"]["ms"] / res["fp64"]["steps"] / hs["ms_per_step"]
+    if args.per_gate_steps > 0:
+        g = run_arm(args, "fp64", world, dist, local, steps=args.per_gate_steps, warmup=1, max_slots=1,
+                    graph=False, e2e_steps=0)
+        pg = arm_summary(g, world)
+        pg["note"] = ("FP64 path with one two-site op in flight (max_slots = 1): the plain per-gate path; "
+                      "1 warm-up step, %d timed" % args.per_gate_steps)
+        line["fp64_per_gate"] = pg
+        line["speedup_mixed_vs_fp64_per_gate"] = pg["ms_per_step"] / hs["ms_per_step"]
+    if args.batched_steps > 0 and args.workload != "batch64_chain16":
+        bt = run_arm(args, hp, world, dist, local, workload="batch64_chain16", steps=args.batched_steps, warmup=1,
+                     graph=False, e2e_steps=0)
+        bs = arm_summary(bt, world)
+        bs.pop("chi_after_warmup", None)
+        bs["note"] = ("64 independent N=16 chains, chi_max from {32, 64, 128, 256} per instance, each started "
+                      "at its saturated chi; %s path, 1 warm-up step, %d timed" % (hp, args.batched_steps))
+        bs["ops_per_step"] = bt["n_ops"]
+        line["batched"] = bs
     if args.adjoint_steps > 0:
         line["adjoint"] = run_adjoint(args, local)
     if rank == 0 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_subprocess(args)
+        line["cpu_baseline"] = cpu_baseline_subprocess(args, "lapack", args.cpu_ops, 1)
+        if not args.no_cpu_plain:
+            line["cpu_baseline_plain"] = cpu_baseline_subprocess(args, "jacobi", 1, 0)
     if rank == 0:
         print(json.dumps(line))
     if dist:

@@ -139,6 +139,27 @@ int mpdo_measure_1q(mpdo_ctx *ctx, const int *qubits, int nq, char comp, double 
 int mpdo_measure_2q(mpdo_ctx *ctx, const int *pairs, int np, const char comp[2], int connected,
                     double *out, int out_on_device);
 
+/* Second Renyi entropy of every instance, Sec. 2.3 Eq. (S_2):
+ * S2 = -ln tr(rho^2) of the normalised rho.  In the orthonormal basis
+ * P_a/sqrt2 tr(rho^2) = <<rho|rho>> / (tr rho)^2, the squared norm of the
+ * coefficient MPS over the squared trace, computed by a left-to-right sweep of
+ * Gram matrices (batched FP64 GEMMs).  out is [B] doubles, host (out_on_device
+ * = 0; the call synchronises) or device.  Uses the per-op workspaces (the state
+ * is untouched).  ESTATE before mpdo_build_gates. */
+int mpdo_renyi2(mpdo_ctx *ctx, double *out, int out_on_device);
+
+/* Operator space entanglement entropy of every instance, Sec. 2.3 Eq. (OSEE):
+ * the von Neumann entropy -sum_k p_k ln p_k, p_k = s_k^2 / sum s^2, of the
+ * normalised vectorised state |rho>> for the cut between path positions bond
+ * and bond + 1 (bond in [0, N-2]; the paper's central bond is N/2 - 1), from
+ * its exact Schmidt values s_k: Gram matrices X, Y of the two halves (batched
+ * FP64 GEMM sweeps), X = F_X^T F_X and Y = F_Y^T F_Y from FP64 Jacobi SVDs, s_k
+ * the singular values of F_X F_Y^T (a third Jacobi SVD).  Independent of the
+ * gauge of the stored tensors.  out as for mpdo_renyi2.  A Jacobi SVD that hits
+ * cfg.jacobi_max_sweeps sets MPDO_ST_NOCONV for its instance (mpdo_status).
+ * EINVAL (bond), ESTATE, ECUDA. */
+int mpdo_osee(mpdo_ctx *ctx, int bond, double *out, int out_on_device);
+
 /* Per-instance status bits (MPDO_ST_*), largest relative discarded weight of
  * any op since the last build_gates, current bond dimensions chi[B][N-1] and
  * the trace before the last normalisation trace_before[B].  Any pointer may

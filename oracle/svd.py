@@ -62,6 +62,15 @@ def jacobi_rows(W: np.ndarray, Z: np.ndarray | None = None, tol: float | None = 
     return sweeps
 
 
+def svd_right_lapack(M: np.ndarray):
+    """The same (s, Vt) as ``svd_right`` from LAPACK's gesdd through numpy,
+    multithreaded by the BLAS under numpy: the route of the paper's solver
+    (threaded LAPACK, Sec. 2.5), timed as a CPU baseline.  Ties in s keep
+    LAPACK's order."""
+    _, s, Vt = np.linalg.svd(np.asarray(M, dtype=np.float64), full_matrices=False)
+    return s, Vt
+
+
 def svd_right(M: np.ndarray, tol: float | None = None):
     """Singular values (descending, stable order) and right singular vectors
     (as rows) of M (m x n), from the one-sided Jacobi above.

@@ -70,7 +70,9 @@ class MPOState:
         return v.reshape(-1)
 
     # -- one two-site op -------------------------------------------------
-    def apply(self, p, G, chi_max, cutoff, forced_k=None, tol=None):
+    def apply(self, p, G, chi_max, cutoff, forced_k=None, tol=None, svd_impl="jacobi"):
+        """One two-site op.  svd_impl = "jacobi" (the oracle's plain C
+        one-sided Jacobi) or "lapack" (numpy's gesdd; CPU timing only)."""
         A, Bn = self.B[p], self.B[p + 1]
         cl, cr = A.shape[0], Bn.shape[2]
         theta = np.einsum("lsm,mtr->lstr", A, Bn)
@@ -78,7 +80,7 @@ class MPOState:
         thetap = np.einsum("abcd,lcdr->labr", G4, theta)
         lam_left = self.lam[p - 1] if p > 0 else np.ones(1)
         tt = (lam_left[:, None, None, None] * thetap).reshape(cl * 4, 4 * cr)
-        s, Vt = svd.svd_right(tt, tol=tol)
+        s, Vt = svd.svd_right(tt, tol=tol) if svd_impl == "jacobi" else svd.svd_right_lapack(tt)
         k = svd.truncation_rank(s, chi_max, cutoff) if forced_k is None else int(forced_k)
         Yk = Vt[:k]
         self.B[p + 1] = Yk.reshape(k, 4, cr).copy()

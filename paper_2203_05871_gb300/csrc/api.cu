@@ -49,7 +49,7 @@ void free_all(mpdo_ctx* c) {
     release_slots(c);
     void* ptrs[] = {c->d_sites, c->d_lam,  c->d_dims,  c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
                     c->d_gates, c->d_specs, c->d_envL,  c->d_envR,   c->d_full,    c->d_one_a, c->d_one_b,
-                    c->d_out,   c->d_q,     c->d_pairs, c->d_need,   c->d_jb_table};
+                    c->d_out,   c->d_q,     c->d_pairs, c->d_need,   c->d_jb_table, c->d_gq};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)

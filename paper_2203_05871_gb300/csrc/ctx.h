@@ -122,6 +122,9 @@ struct mpdo_ctx {
     // autotuned Jacobi rows per block: [(chi_l * (cap+1) + chi_r) * 2 + fp32], 0 = the default rule
     std::vector<int> jb_table;
     int* d_jb_table = nullptr;
+    // descriptors of the Gram-matrix GEMM sweeps (global.cu), grown on demand
+    mpdo::GemmDesc* d_gq = nullptr;
+    size_t gq_cap = 0;
     // host-side fault injection (mpdo_inject_fault): MPDO_FAULT_* of the next QR launch, 0 = none
     int inject = 0;
     // profiling

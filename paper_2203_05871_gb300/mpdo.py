@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
                                                    ctypes.c_int, ctypes.c_char, vp, vp]),
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
         "mpdo_inject_fault": (ctypes.c_int, [vp, ctypes.c_int]),
+        "mpdo_renyi2": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "mpdo_osee": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
         "mpdo_autotune": (ctypes.c_int, [vp, _ip, ctypes.c_int, _ip]),
         "mpdo_grad_forward": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_grad_backward": (ctypes.c_int, [vp, _dp, _dp, _dp, _dp]),
@@ -111,7 +113,7 @@ def exported_symbols() -> list[str]:
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
-            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_grad_forward",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_renyi2", "mpdo_osee", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -257,6 +259,21 @@ class Solver:
         res = np.zeros((self.batch, len(p)))
         _check(self._lib.mpdo_measure_2q(self._h, _ptr(p, ctypes.c_int), len(p), comps.encode(), int(connected),
                                          res.ctypes.data_as(ctypes.c_void_p), 0))
+        return res
+
+    def renyi2(self):
+        """Second Renyi entropy S2 = -ln tr(rho^2) of every instance, [B]."""
+        res = np.zeros(self.batch)
+        _check(self._lib.mpdo_renyi2(self._h, res.ctypes.data_as(ctypes.c_void_p), 0))
+        return res
+
+    def osee(self, bond: Optional[int] = None):
+        """Operator space entanglement entropy at the cut after path position
+        ``bond`` (default: the central bond N/2 - 1), [B]."""
+        if bond is None:
+            bond = self.n // 2 - 1
+        res = np.zeros(self.batch)
+        _check(self._lib.mpdo_osee(self._h, int(bond), res.ctypes.data_as(ctypes.c_void_p), 0))
         return res
 
     # -- state and diagnostics ------------------------------------------

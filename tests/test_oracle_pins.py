@@ -352,3 +352,19 @@ def test_frozen_rank_replay_reproduces_run():
     t2 = tebd.TEBD(wl).run(3, forced_k=list(t1.k_log))
     np.testing.assert_allclose(t1.z(), t2.z(), atol=1e-14)
     assert t1.k_log == t2.k_log
+
+
+def test_lapack_route_matches_jacobi_route():
+    """The oracle's LAPACK SVD route (the CPU baseline of the paper's threaded
+    LAPACK solver) keeps the same state as its plain Jacobi route."""
+    wl = W.random_model(6, W.chain_bonds(6), 23, chi_max=8, cutoff=1e-12, dt=0.2)
+    a = tebd.TEBD(wl)
+    b = tebd.TEBD(wl)
+    for _ in range(4):
+        for layer, gl in zip(a.layers, a.gates):
+            for op, G in zip(layer, gl):
+                ka, _ = a.state.apply(op[1], G, 8, 1e-12)
+                kb, _ = b.state.apply(op[1], G, 8, 1e-12, forced_k=ka, svd_impl="lapack")
+        a.state.normalize_trace()
+        b.state.normalize_trace()
+    assert np.abs(a.z() - b.z()).max() < 1e-10
