@@ -73,9 +73,10 @@ def parse():
 
 # ---------------------------------------------------------------------------
 # Schmidt-value grading of the synthetic start: exp(-DECAY * r) on bond index r,
-# i.e. about 1e-5 between the first and the 256th value (a discarded weight
-# near the 1e-10 cutoff at chi = 256)
-DECAY = 0.045
+# i.e. about 6e-3 between the first and the 256th value, so that the 1e-10
+# cutoff never binds before chi_max = 256 and every inner bond of the chain
+# stays saturated through the timed steps
+DECAY = 0.02
 
 
 def make_workload(name):
@@ -179,10 +180,11 @@ def cpu_info():
             "machine": platform.machine()}
 
 
-def oracle_ops(wl, dims, tens, count, warm, svd_impl):
+def oracle_ops(wl, dims, tens, count, warm, svd_impl, full_size_only=False):
     """Time the oracle's two-site update on the workload's ops in step order
-    (cycling), each from the saturated start state.  Returns (per-op seconds of
-    the timed ops, description)."""
+    (cycling), each from the saturated start state; full_size_only keeps the
+    ops whose bond matrix is (4 chi_max) x (4 chi_max).  Returns (per-op seconds
+    of the timed ops, description)."""
     import numpy as np
     from oracle import schedule, tebd
     layers = schedule.step_layers(wl.n, wl.bonds)
@@ -190,6 +192,8 @@ def oracle_ops(wl, dims, tens, count, warm, svd_impl):
     ops = [(op[1], G) for L, gl in zip(layers, gates) for op, G in zip(L, gl)]
     st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
     cap = int(wl.chi_max[0])
+    if full_size_only:
+        ops = [(p, G) for (p, G) in ops if dims[p] == cap and dims[p + 2] == cap] or ops
     times, sizes = [], []
     for r in range(warm + count):
         p, G = ops[r % len(ops)]
@@ -213,7 +217,8 @@ def run_reference(args):
     b = next(i for i in range(wl.batch) if int(wl.chi_max[i]) == cap)   # an instance at full chi
     dims, tens = states[b]
     threads = os.cpu_count() if args.oracle_svd == "lapack" else 1
-    times, what = oracle_ops(wl.instance(b), dims, tens, args.steps, args.warmup, args.oracle_svd)
+    times, what = oracle_ops(wl.instance(b), dims, tens, args.steps, args.warmup, args.oracle_svd,
+                             full_size_only=args.oracle_svd == "jacobi")
     v = len(times) / sum(times)
     info = cpu_info()
     line = {"impl": "reference", "metric": "gate_applications_per_sec", "value": v,

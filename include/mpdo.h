@@ -278,6 +278,22 @@ int mpdo_profile_sweeps_critical(mpdo_ctx *ctx, long long *crit, long long *crit
 int mpdo_measure_1q_noalloc(const double *sites, const int *dims, int n_qubits, int batch, int chi_cap,
                             const int *qubits, int nq, char comp, double *out, void *cuda_stream);
 
+/* C = A B with FP64 semantics on the tensor cores: the product the mixed path
+ * uses for its contractions and SVD-preconditioner GEMMs, on caller matrices
+ * (the paper has none; its contractions are FP64 ITensor/LAPACK calls).  Each
+ * row of A and column of B is scaled by a power of two and cut into six 8-bit
+ * slices, exact in tf32 (kind = MPDO_MIXED_TF32) or bf16 (MPDO_MIXED_BF16X3);
+ * the 21 slice products of the leading levels are formed by tcgen05 MMAs with
+ * error-free FP32 accumulation per 256 values of K and summed in FP64, so the
+ * error is about 2^-46 |A_i|max |B_j|max per term of the sum.
+ *   A  device, M x K row-major (lda >= K);  B  device, K x N (ldb >= N);
+ *   C  device, M x N (ldc >= N), overwritten.
+ * Allocates its slice scratch (cudaMalloc) per call and synchronises the
+ * stream.  A non-finite entry makes its row of C (A) or column (B) NaN.
+ * EINVAL (sizes, kind), ENOMEM, ECUDA. */
+int mpdo_gemm_tc(int M, int N, int K, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+                 int kind, void *cuda_stream);
+
 /* Reverse-mode gradient of the observables with respect to the model
  * parameters (the paper has no gradient; this differentiates the update of
  * App. B as implemented here, with the ranks of the forward run held fixed).

@@ -61,8 +61,10 @@ void free_all(mpdo_ctx* c) {
 }
 
 int release_slots(mpdo_ctx* c) {
-    void* ptrs[] = {c->d_thetap, c->d_W, c->d_Z, c->d_Yk, c->d_snorm, c->d_desc, c->d_cta, c->d_sync, c->d_sweeps,
-                    c->d_pre_ok, c->d_W0, c->d_E, c->d_Q, c->d_W32, c->d_U32, c->d_gemm, c->d_copy};
+    void* ptrs[] = {c->d_thetap, c->d_W,    c->d_Z,     c->d_Yk,    c->d_snorm, c->d_desc,  c->d_cta,
+                    c->d_sync,   c->d_sweeps, c->d_pre_ok, c->d_W0,  c->d_E,     c->d_Q,     c->d_W32,
+                    c->d_U32,    c->d_gemm,  c->d_copy,  c->d_oz_as, c->d_oz_bs, c->d_oz_ea, c->d_oz_eb,
+                    c->d_oz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
@@ -70,6 +72,9 @@ int release_slots(mpdo_ctx* c) {
     c->d_W32 = c->d_U32 = nullptr;
     c->d_gemm = nullptr;
     c->d_copy = nullptr;
+    c->d_oz_as = c->d_oz_bs = nullptr;
+    c->d_oz_ea = c->d_oz_eb = nullptr;
+    c->d_oz = nullptr;
     if (c->h_gemm) cudaFreeHost(c->h_gemm);
     c->h_gemm = nullptr;
     if (c->h_copy) cudaFreeHost(c->h_copy);
@@ -95,7 +100,11 @@ int alloc_slots(mpdo_ctx* c, int want) {
     release_slots(c);
     const size_t mat = (size_t)c->ld * c->ld;
     size_t per_slot_bytes = (3 * mat + (size_t)c->cap * c->ld + 2 * c->ld) * sizeof(double);
-    if (c->mixed) per_slot_bytes += 3 * mat * sizeof(double) + 2 * mat * sizeof(float);
+    if (c->mixed) {
+        c->oz_slot_bytes = oz_slice_bytes(c->ld, c->ld, c->oz_bf16);
+        per_slot_bytes += 3 * mat * sizeof(double) + 2 * mat * sizeof(float) + 2 * c->oz_slot_bytes +
+                          2 * (size_t)c->ld * sizeof(int);
+    }
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
     const size_t budget = free_b / 2;
@@ -126,8 +135,11 @@ int alloc_slots(mpdo_ctx* c, int want) {
         CU(dalloc(&c->d_Q, (size_t)s * mat));
         CU(dalloc(&c->d_W32, (size_t)s * mat));
         CU(dalloc(&c->d_U32, (size_t)s * mat));
-        CU(dalloc(&c->d_gemm, (size_t)3 * s));
-        CU(cudaMallocHost((void**)&c->h_gemm, sizeof(GemmDesc) * 3 * s));
+        CU(dalloc(&c->d_oz_as, (size_t)s * c->oz_slot_bytes));
+        CU(dalloc(&c->d_oz_bs, (size_t)s * c->oz_slot_bytes));
+        CU(dalloc(&c->d_oz_ea, (size_t)s * c->ld));
+        CU(dalloc(&c->d_oz_eb, (size_t)s * c->ld));
+        CU(dalloc(&c->d_oz, (size_t)s));
     }
     return MPDO_OK;
 }
@@ -262,6 +274,10 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
     d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
     d.Zinit = nullptr;
+    d.oz_as = c->mixed ? c->d_oz_as + (size_t)s * c->oz_slot_bytes : nullptr;
+    d.oz_bs = c->mixed ? c->d_oz_bs + (size_t)s * c->oz_slot_bytes : nullptr;
+    d.oz_ea = c->mixed ? c->d_oz_ea + (size_t)s * ld : nullptr;
+    d.oz_eb = c->mixed ? c->d_oz_eb + (size_t)s * ld : nullptr;
 }
 
 int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,
@@ -311,11 +327,14 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         const double nn = 4.0 * std::max(d.cl, d.cr);
         fl_svd += 21.0 * nn * nn * nn;
     }
+    const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
     ProfScope p_merge(c, K_MERGE);
-    if (c->mixed)
-        CU(launch_tc_merge_gate(c->d_desc, nops, cap, c->st));
-    else
+    if (c->mixed) {
+        CU(launch_oz_ops(c->d_desc, nops, OZ_MERGE, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
+        CU(launch_gate_weight(c->d_desc, nops, cap, c->st));
+    } else {
         CU(launch_merge_gate(c->d_desc, nops, cap, c->st));
+    }
     p_merge.stop();
     if (tape) {
         int nc = 0, max_rows = 1;
@@ -327,7 +346,6 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         CU(launch_copy2d(c->d_copy + nc, nops, max_rows, c->st));
     }
 
-    const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
     const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), c->slots);
     double qr_flops_chunk = 0.0;
     // Jacobi launch plan: share the co-resident CTAs among the ops in
@@ -410,27 +428,16 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         int rc = run_jacobi(true, 1);
         if (rc) return rc;
         p_j32.stop();
-        // E = U U^T - I (FP64 accumulation of exact FP32 products),
-        // Q = U - E U / 2 (one Newton-Schulz step; E is ~1e-6 so FP32 suffices),
-        // W = Q W0 (FP64)
-        GemmDesc* g1 = c->h_gemm;
-        GemmDesc* g2 = c->h_gemm + c->slots;
-        GemmDesc* g3 = c->h_gemm + 2 * c->slots;
-        int maxc = 1, maxL = 1;
+        // E = U U^T - I, Q = U - E U / 2 (one Newton-Schulz step), W = Q W0, all
+        // FP64-accurate tensor-core products (oz_gemm.cu)
         for (int s = 0; s < nops; ++s) {
             const OpDesc& d = c->h_desc[s];
-            maxc = std::max(maxc, d.c);
-            maxL = std::max(maxL, d.L);
-            g1[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0, 1};
-            g2[s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0, 0};
-            g3[s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0, 0};
             fl_gemm += 2.0 * d.c * d.c * d.c * 2 + 2.0 * d.c * d.c * d.L;
         }
-        CU(cudaMemcpyAsync(c->d_gemm, c->h_gemm, sizeof(GemmDesc) * 3 * c->slots, cudaMemcpyHostToDevice, c->st));
         ProfScope p_gemm(c, K_GEMM);
-        CU(launch_gemm(c->d_gemm, nops, maxc, maxc, false, c->st));
-        CU(launch_gemm(c->d_gemm + c->slots, nops, maxc, maxc, true, c->st));
-        CU(launch_gemm(c->d_gemm + 2 * c->slots, nops, maxc, maxL, false, c->st));
+        CU(launch_oz_ops(c->d_desc, nops, OZ_E, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
+        CU(launch_oz_ops(c->d_desc, nops, OZ_Q, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
+        CU(launch_oz_ops(c->d_desc, nops, OZ_W, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
         p_gemm.stop();
     }
     ProfScope p_jac(c, K_JACOBI);
@@ -444,7 +451,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
     p_tr.stop();
     ProfScope p_rec(c, K_RECON);
     if (c->mixed)
-        CU(launch_tc_reconstruct(c->d_desc, nops, cap, c->st));
+        CU(launch_oz_ops(c->d_desc, nops, OZ_RECON, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
     else
         CU(launch_reconstruct(c->d_desc, nops, cap, c->st));
     p_rec.stop();
@@ -580,10 +587,8 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     if (cfg->n_qubits < 3) return fail(MPDO_EINVAL, "n_qubits must be >= 3");
     if (cfg->batch < 1) return fail(MPDO_EINVAL, "batch must be >= 1");
     if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
-    if (cfg->precision == MPDO_MIXED_BF16X3)
-        return fail(MPDO_EINVAL, "MPDO_MIXED_BF16X3 is not built yet");
-    if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32)
-        return fail(MPDO_EINVAL, "precision must be MPDO_FP64 or MPDO_MIXED_TF32");
+    if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32 && cfg->precision != MPDO_MIXED_BF16X3)
+        return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
     if (cfg->storage != MPDO_STORE_F64 && cfg->storage != MPDO_STORE_F32)
         return fail(MPDO_EINVAL, "storage must be MPDO_STORE_F64 or MPDO_STORE_F32");
     if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
@@ -597,6 +602,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     if (!c) return fail(MPDO_ENOMEM, "host allocation failed");
     c->dev = dev;
     c->mixed = cfg->precision != MPDO_FP64;
+    c->oz_bf16 = cfg->precision == MPDO_MIXED_BF16X3;
     c->cfg = *cfg;
     c->st = (cudaStream_t)cuda_stream;
     c->N = cfg->n_qubits;
@@ -629,7 +635,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
              std::string("device allocation: ") + cudaGetErrorString(e));
         return bail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA);
     }
-    if ((e = tc_prepare()) != cudaSuccess) {
+    if ((e = oz_prepare()) != cudaSuccess) {
         fail(MPDO_ECUDA, std::string("tensor-core kernel set-up: ") + cudaGetErrorString(e));
         return bail(MPDO_ECUDA);
     }

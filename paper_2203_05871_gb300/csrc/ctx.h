@@ -87,6 +87,11 @@ struct mpdo_ctx {
     int* d_sweeps = nullptr;      // [slots] Jacobi sweeps of the last chunk
     int* d_pre_ok = nullptr;      // [slots] mixed path: the FP32 pass ended by its off-orthogonality rule
     bool mixed = false;           // mixed-precision SVD (FP32 preconditioning + FP64 finish)
+    bool oz_bf16 = false;         // mixed path: tensor-core slices in bf16 (MPDO_MIXED_BF16X3), else tf32
+    unsigned char *d_oz_as = nullptr, *d_oz_bs = nullptr;   // [slots] slice blocks of the tensor-core products
+    int *d_oz_ea = nullptr, *d_oz_eb = nullptr;             // [slots][4 chi_cap] their exponents
+    mpdo::OzProblem* d_oz = nullptr;                        // [slots] problems of one launch
+    size_t oz_slot_bytes = 0;
     double *d_W0 = nullptr, *d_E = nullptr, *d_Q = nullptr;
     float *d_W32 = nullptr, *d_U32 = nullptr;
     mpdo::GemmDesc* d_gemm = nullptr;

@@ -44,10 +44,10 @@ __global__ void gram_unit_kernel(double* W, size_t mat, int m) {
     W[(size_t)i * mat] = 1.0;
 }
 
-// norms[s * 2 ld + j] = |row j| of the matrix in slot s (rows j < chi[s / 2])
+// norms[s * 2 ld + j] = |row j| of the matrix in slot s (rows j < chi[s])
 __global__ void row_norms_kernel(const double* W, size_t mat, int ld, const int* chi, double* norms) {
     const int s = blockIdx.y;
-    const int n = chi[s / 2];
+    const int n = chi[s];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double* M = W + (size_t)s * mat;
     for (int j = blockIdx.x * 8 + warp; j < n; j += gridDim.x * 8) {

@@ -6,8 +6,9 @@
 // reads the bond dimensions on the device and writes the dimension fields of
 // the chunk's op descriptors, the co-resident CTA plans of the cooperative QR
 // and Jacobi launches (the host plan's proportional-to-work rule; the launch
-// has every resident CTA and the unassigned ones return at once) and the
-// preconditioner GEMM shapes; every other launch has a capacity-sized grid
+// has every resident CTA and the unassigned ones return at once); the
+// tensor-core products build their problem shapes from the descriptors on the
+// device as well, and every other launch has a capacity-sized grid
 // whose CTAs outside an op's shape return at once.  The step is captured once
 // per layout (op list and workspaces) and replayed; ranks are collected on the
 // device.
@@ -67,9 +68,8 @@ __device__ int plan_ctas(const double* work, const int* cap, int nops, int R, in
 constexpr int kMaxChunk = 1024;
 
 __global__ void __launch_bounds__(256) plan_chunk_kernel(OpDesc* descs, int nops, const int* dims, int N, int Rj,
-                                                         int Rq, int* cta64, int* cta32, int* ctaqr, GemmDesc* gemm,
-                                                         int ld, int mixed, const int* jb_table, int chi_cap,
-                                                         int* error) {
+                                                         int Rq, int* cta64, int* cta32, int* ctaqr, int mixed,
+                                                         const int* jb_table, int chi_cap, int* error) {
     __shared__ double work[kMaxChunk];
     __shared__ int cap[kMaxChunk];
     for (int s = threadIdx.x; s < nops; s += blockDim.x) {
@@ -88,11 +88,6 @@ __global__ void __launch_bounds__(256) plan_chunk_kernel(OpDesc* descs, int nops
             const int* t = jb_table + ((size_t)d.cl * (chi_cap + 1) + d.cr) * 2;
             if (t[0] > 0) d.jb = t[0];
             if (t[1] > 0) d.jb32 = t[1];
-        }
-        if (mixed) {
-            gemm[s] = GemmDesc{d.c, d.c, d.c, d.U32, ld, 1, d.U32, ld, 1, 1, d.E, ld, 1.0, 0.0, nullptr, 0, 0, 1, 0, 1};
-            gemm[nops + s] = GemmDesc{d.c, d.c, d.c, d.E, ld, 0, d.U32, ld, 1, 0, d.Q, ld, -0.5, 1.0, d.U32, ld, 1, 0, 0};
-            gemm[2 * nops + s] = GemmDesc{d.c, d.L, d.c, d.Q, ld, 0, d.W0, ld, 0, 0, d.W, ld, 1.0, 0.0, nullptr, 0, 0, 0, 0};
         }
     }
     __syncthreads();
@@ -129,7 +124,6 @@ struct Chunk {
     int nops = 0;
     OpDesc* d_desc = nullptr;
     int *d_cta64 = nullptr, *d_cta32 = nullptr, *d_ctaqr = nullptr;
-    GemmDesc* d_gemm = nullptr;
 };
 
 }  // namespace
@@ -154,7 +148,7 @@ void release(GraphState* g) {
     g->graph = nullptr;
     for (auto& L : g->chunks)
         for (auto& ch : L) {
-            void* ptrs[] = {ch.d_desc, ch.d_cta64, ch.d_cta32, ch.d_ctaqr, ch.d_gemm};
+            void* ptrs[] = {ch.d_desc, ch.d_cta64, ch.d_cta32, ch.d_ctaqr};
             for (void* p : ptrs)
                 if (p) cudaFree(p);
         }
@@ -174,14 +168,16 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
         for (auto& ch : L) {
             const int nops = ch.nops;
             plan_chunk_kernel<<<1, 256, 0, st>>>(ch.d_desc, nops, c->d_dims, c->N, g->Rj, g->Rq, ch.d_cta64,
-                                                 ch.d_cta32, ch.d_ctaqr, ch.d_gemm, ld, c->mixed ? 1 : 0,
-                                                 c->d_jb_table, cap, g->d_error);
+                                                 ch.d_cta32, ch.d_ctaqr, c->mixed ? 1 : 0, c->d_jb_table, cap,
+                                                 g->d_error);
             CU(cudaGetLastError());
             CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, st));
-            if (c->mixed)
-                CU(launch_tc_merge_gate(ch.d_desc, nops, cap, st));
-            else
+            if (c->mixed) {
+                CU(launch_oz_ops(ch.d_desc, nops, OZ_MERGE, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
+                CU(launch_gate_weight(ch.d_desc, nops, cap, st));
+            } else {
                 CU(launch_merge_gate(ch.d_desc, nops, cap, st));
+            }
             const size_t sync_bytes = sizeof(unsigned) * jacobi_sync_words_per_op() * nops;
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
             CU(launch_qr(ch.d_desc, ch.d_ctaqr, ch.d_ctaqr + g->Rq, ch.d_ctaqr + 2 * g->Rq, c->d_sync, g->Rq,
@@ -190,16 +186,16 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
                 CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
                 CU(launch_jacobi(ch.d_desc, nops, ch.d_cta32, ch.d_cta32 + g->Rj, ch.d_cta32 + 2 * g->Rj, c->d_sync,
                                  g->Rj, kMaxSweepsCap / 2, 0.0, timeout_ns, ld, true, st));
-                CU(launch_gemm(ch.d_gemm, nops, ld, ld, false, st));
-                CU(launch_gemm(ch.d_gemm + nops, nops, ld, ld, true, st));
-                CU(launch_gemm(ch.d_gemm + 2 * nops, nops, ld, ld, false, st));
+                CU(launch_oz_ops(ch.d_desc, nops, OZ_E, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
+                CU(launch_oz_ops(ch.d_desc, nops, OZ_Q, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
+                CU(launch_oz_ops(ch.d_desc, nops, OZ_W, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
             }
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
             CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync, g->Rj,
                              c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
             CU(launch_truncate(ch.d_desc, nops, cap, st));
             if (c->mixed)
-                CU(launch_tc_reconstruct(ch.d_desc, nops, cap, st));
+                CU(launch_oz_ops(ch.d_desc, nops, OZ_RECON, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
             else
                 CU(launch_reconstruct(ch.d_desc, nops, cap, st));
             klog_kernel<<<(nops + 127) / 128, 128, 0, st>>>(ch.d_desc, nops, c->n_ops, g->d_klog);
@@ -233,10 +229,7 @@ int build_graph(mpdo_ctx* c, GraphState* g) {
             CU(dalloc(&ch.d_desc, (size_t)nops));
             CU(dalloc(&ch.d_cta64, (size_t)2 * g->Rj + nops));
             CU(dalloc(&ch.d_ctaqr, (size_t)2 * g->Rq + nops));
-            if (c->mixed) {
-                CU(dalloc(&ch.d_cta32, (size_t)2 * g->Rj + nops));
-                CU(dalloc(&ch.d_gemm, (size_t)3 * nops));
-            }
+            if (c->mixed) CU(dalloc(&ch.d_cta32, (size_t)2 * g->Rj + nops));
             CU(cudaMemcpyAsync(ch.d_desc, h.data(), sizeof(OpDesc) * nops, cudaMemcpyHostToDevice, c->st));
             CU(cudaStreamSynchronize(c->st));
             g->chunks[li].push_back(ch);

@@ -78,6 +78,8 @@ struct OpDesc {
     int full_svd;      // 1: orthogonalise every pair of rows (the adjoint needs all singular vectors)
     double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr
     double* tape_s;    // adjoint recompute: all c sorted singular values
+    void *oz_as, *oz_bs;   // mixed path: slice blocks of the tensor-core products (oz_gemm.cu)
+    int *oz_ea, *oz_eb;    // and their row / column exponents
 };
 
 // Site tensor element i as double (storage f64 or f32), and the store back.
@@ -156,12 +158,51 @@ size_t jacobi_sync_words_per_op();
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
 
-// tensor-core (tcgen05 kind::tf32, 3xTF32 split) merge+gate and reconstruct
-cudaError_t tc_prepare();
-cudaError_t launch_tc_merge_gate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
-cudaError_t launch_tc_reconstruct(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
-uint32_t tc_instr_desc_tf32(int M, int N);
-uint64_t tc_smem_desc(uint32_t saddr);
+// ---------------------------------------------------------------------------
+// FP64-accurate GEMM on the tensor cores from exact slice products (oz_gemm.cu)
+// ---------------------------------------------------------------------------
+// One operand as a view over (row, k): A's rows are the rows i of A, B's rows
+// the columns j of B.  mode 0: element (r, k) at base[r * rs + k * ks];
+// mode 1 (right site of a merge): element (n, k) at base[(k * 4 + n / cr) * cap + n % cr].
+struct OzOperand {
+    const void* base;
+    int f32;             // elements are float (else double)
+    long long rs, ks;
+    int mode, cr, cap;
+};
+// C = alpha A B + beta D (- I), C and D row-major (f64 or f32)
+struct OzProblem {
+    int M, N, K;
+    const int* Ndyn;     // non-null: N is read on the device (<= N, which sizes the tiles)
+    OzOperand A, B;
+    void* C;
+    int ldc, c_f32;
+    double alpha, beta;
+    const void* D;
+    int ldd, d_f32, sub_identity;
+    void *as, *bs;       // slice blocks of A and B
+    int *ea, *eb;        // row / column exponents
+    int Mt, Nt, Kt;      // tiles (128 rows, 128 columns, 64 bytes of K)
+    int* status;         // MPDO_ST_TIMEOUT when a wait gives up (or nullptr)
+};
+size_t oz_slice_bytes(int rows, int K, bool bf16);
+void oz_tiles(OzProblem& p, bool bf16);
+cudaError_t oz_prepare();
+// slices both operands of count problems, then multiplies; max_m / max_n /
+// max_rows_sliced bound the grids (CTAs outside a problem's tiles return)
+cudaError_t launch_oz_gemm(const OzProblem* d_probs, int count, int max_m, int max_n, int max_rows_sliced, bool bf16,
+                           unsigned long long timeout_ns, cudaStream_t st);
+
+// The mixed path's tensor-core products of a chunk of ops, built on the
+// device from the op descriptors (so the host-planned and the graph step
+// share them): kind OZ_MERGE Theta = A B (then launch_gate_weight applies the
+// gate and the left weights), OZ_RECON B_p' = Theta' Yk^T, OZ_E E = U U^T - I,
+// OZ_Q Q = U - E U / 2, OZ_W W = Q W0.  probs: scratch for nops problems.
+enum { OZ_MERGE = 0, OZ_RECON = 1, OZ_E = 2, OZ_Q = 3, OZ_W = 4 };
+cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* probs, int chi_cap, bool bf16,
+                          unsigned long long timeout_ns, cudaStream_t st);
+// Theta' = G Theta in place in thetap and theta~ = lambda_l Theta' (column-major, Acm)
+cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
 
 int qr_threads();
 cudaError_t qr_max_resident(int* blocks);

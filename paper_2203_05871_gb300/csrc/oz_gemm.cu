@@ -1,0 +1,648 @@
+// FP64-accurate batched GEMM on the tcgen05 tensor cores (the mixed path's
+// contractions and its SVD-preconditioner products).
+//
+//   C = alpha * A B + beta * D  (- I when sub_identity),  A: M x K, B: K x N,
+// FP64 (or f32) in and out, computed from exact products of narrow slices of
+// the operands (the error-free splitting of Ozaki, Ogita, Oishi & Rump,
+// "Error-free transformations of matrix multiplication by using fast routines
+// of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
+//
+// 1. Slicing (oz_slice_kernel).  Each row i of A is scaled by 2^-e_i, e_i the
+//    binary exponent of its largest |A_ik| (so |a| < 1), and cut into S = 6
+//    slices a = 2^-7 sum_t sigma_t 2^-8t with integers |sigma_t| <= 128
+//    (sigma_0 = rint(128 a), each later slice the rint of 256 x the
+//    remainder); a slice keeps 8 significant bits, so it is exact in bf16
+//    (MPDO_MIXED_BF16X3) and in tf32 (MPDO_MIXED_TF32), and it is stored as
+//    sigma_t 2^-8t.  B is cut the same way per column j (exponent f_j).  The
+//    remainder after six slices is below 2^-48 of the row's largest entry.
+// 2. Products (oz_gemm_kernel).  Every slice pair (t, u) with t + u <= 5 is
+//    multiplied on the tensor core: a product sigma_t sigma_u has at most 16
+//    bits, so it is exact in FP32, and the sums stay exact while they fit 24
+//    bits.  Four accumulators in tensor memory, each product already at its
+//    own scale 2^-8(t+u) through the stored slices: level 0 (pair (0,0)),
+//    level 1 ((0,1), (1,0)), level 2 (three pairs) and level 3+ (the fifteen
+//    pairs of levels 3-5).  Every 256 values of K the accumulators are drained
+//    into FP64 registers: 256 products of up to 2^14 fit 2^22, so levels 0, 1
+//    and 2 (at most three pairs) are summed without any rounding; level 3+
+//    rounds at 2^-24 of itself, about 2^-46 of the result.
+// 3. Epilogue: C_ij = alpha 2^(e_i + f_j - 14) (L0 + L1 + L2 + L3) + beta D_ij.
+// Error: about 2^-46 |A_i|_max |B_j|_max per term of the sum (a numpy model of
+// the scheme: 6e-14 normwise on 1024 x 1024 x 1024, graded or not), against
+// FP64's 2^-53 |A_ik B_kj|: FP64-class accuracy at tensor-core speed.
+//
+// Data layout.  The slices are written in the tcgen05 canonical K-major,
+// no-swizzle layout, pre-tiled: a block of 128 rows x 64 bytes of K (32 bf16 or
+// 16 tf32 values) is 8 KB, element (row, k) at (row/8)*512 + (k/g)*128 +
+// (row%8)*16 + (k%g)*esize, g = 16/esize (core matrices of 8 rows x 16 bytes,
+// LBO = 128 B along K, SBO = 512 B along rows), so one cp.async.bulk moves a
+// block into shared memory as it is.  Blocks are [slice][row tile][k tile].
+//
+// Kernel.  One CTA per 128 x 128 tile of C, 320 threads: warp 0 issues the
+// bulk copies of the 6 + 6 slice blocks of each k tile into a 2-stage ring
+// (96 KB per stage), warp 1 issues the 42 MMAs of a k tile (21 pairs x 2
+// instructions of K = 16 bf16 / 8 tf32; M = 128, N = 128) and commits, warps
+// 2-9 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .. +31, its
+// half of the 128 columns).  Every wait is bounded by timeout_ns; a wait that
+// gives up records MPDO_ST_TIMEOUT in the problem's status word, the other roles
+// leave their loops at the next poll, outstanding copies and MMAs are waited
+// for (bounded) and the tensor memory is released before the CTA returns.
+#include <mpdo.h>
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace mpdo {
+
+namespace {
+
+constexpr int kS = 6;                  // slices per operand
+constexpr int kPairs = 21;             // (t, u) with t + u <= 5
+constexpr int kLevels = 4;             // accumulators: levels 0, 1, 2 and 3+
+constexpr int kBlock = 8192;           // bytes of one 128-row x 64-byte slice block
+constexpr int kTileRows = 128;
+constexpr int kStageBytes = 2 * kS * kBlock;   // A and B slices of one k tile
+constexpr int kStages = 2;
+constexpr int kRangeK = 256;           // K values between accumulator drains
+constexpr int kThreads = 320;
+constexpr int kSmem = kStages * kStageBytes + 1024;
+constexpr int LBO = 128, SBO = 512;
+
+__host__ __device__ constexpr int kt_elems(int esize) { return 64 / esize; }
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+    // start >> 4 (bits 0-13), LBO >> 4 (16-29), SBO >> 4 (32-45), version 1 (46-47), no swizzle
+    return (uint64_t)((saddr & 0x3FFFF) >> 4) | ((uint64_t)(LBO >> 4) << 16) | ((uint64_t)(SBO >> 4) << 32) |
+           (1ull << 46);
+}
+
+// D = F32 (bits 4-5 = 1); A, B = BF16 (1) or TF32 (2) at bits 7-9, 10-12; K-major;
+// N >> 3 at bits 17-22; M >> 4 at bits 24-28
+__host__ __device__ constexpr uint32_t idesc(bool bf16, int M, int N) {
+    const uint32_t ab = bf16 ? 1u : 2u;
+    return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// bounded wait; false when it gave up (timeout) or another role aborted
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long timeout_ns) {
+    const unsigned long long t0 = gtimer();
+    for (int it = 0;; ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((it & 63) == 63) {
+            if (*abort_flag) return false;
+            if (gtimer() - t0 > timeout_ns) {
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void mma(bool bf16, uint32_t dtmem, uint64_t a, uint64_t b, uint32_t id,
+                                    uint32_t accumulate) {
+    if (bf16)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+            "l"(a), "l"(b), "r"(id), "r"(accumulate));
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+            "l"(a), "l"(b), "r"(id), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ int pair_t(int p) {   // pairs in order of level: (0,0) (0,1)(1,0) (0,2)(1,1)(2,0) ...
+    constexpr int T[kPairs] = {0, 0, 1, 0, 1, 2, 0, 1, 2, 3, 0, 1, 2, 3, 4, 0, 1, 2, 3, 4, 5};
+    return T[p];
+}
+__device__ __forceinline__ int pair_u(int p) {
+    constexpr int U[kPairs] = {0, 1, 0, 2, 1, 0, 3, 2, 1, 0, 4, 3, 2, 1, 0, 5, 4, 3, 2, 1, 0};
+    return U[p];
+}
+
+// element r, k of an operand view (double)
+__device__ __forceinline__ double oz_load(const OzOperand& X, int r, int k) {
+    size_t i;
+    if (X.mode == 1)
+        i = ((size_t)k * 4 + (size_t)(r / X.cr)) * X.cap + (r % X.cr);
+    else
+        i = (size_t)r * X.rs + (size_t)k * X.ks;
+    return X.f32 ? (double)static_cast<const float*>(X.base)[i] : static_cast<const double*>(X.base)[i];
+}
+
+// The slices of G consecutive values x[0..G) of one row (exponent e), stored
+// as 16 bytes per slice.
+template <int G, bool kBf16>
+__device__ __forceinline__ void slice_group(const double* x, int e, uint4* out /* [kS] */) {
+    double rem[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) rem[g] = ldexp(x[g], 7 - e);   // |rem| < 128
+#pragma unroll
+    for (int t = 0; t < kS; ++t) {
+        float sl[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const double q = rint(rem[g]);
+            rem[g] = (rem[g] - q) * 256.0;                         // exact: |rem - q| <= 1/2
+            sl[g] = (float)ldexp(q, -8 * t);                       // <= 8 significant bits: exact
+        }
+        if constexpr (kBf16) {
+            uint32_t w[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 p = __floats2bfloat162_rn(sl[2 * h], sl[2 * h + 1]);
+                w[h] = *reinterpret_cast<const uint32_t*>(&p);
+            }
+            out[t] = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+            out[t] = make_uint4(__float_as_uint(sl[0]), __float_as_uint(sl[1]), __float_as_uint(sl[2]),
+                                __float_as_uint(sl[3]));
+        }
+    }
+}
+
+// grid (row groups of 8, 2 = A | B, problems); one warp per row of the operand
+template <bool kBf16>
+__global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
+    constexpr int esize = kBf16 ? 2 : 4;
+    constexpr int G = 16 / esize;          // values per 16-byte store
+    constexpr int KT = kt_elems(esize);
+    const OzProblem& P = probs[blockIdx.z];
+    const bool isB = blockIdx.y == 1;
+    const OzOperand& X = isB ? P.B : P.A;
+    const int N = P.Ndyn ? *P.Ndyn : P.N;
+    const int R = isB ? N : P.M;
+    const int Rt = isB ? P.Nt : P.Mt;
+    const int K = P.K, Kt = P.Kt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * 8 + warp;
+    if (r >= Rt * kTileRows) return;
+    unsigned char* out = static_cast<unsigned char*>(isB ? P.bs : P.as);
+    int* ex = isB ? P.eb : P.ea;
+    const bool live = r < R;
+    double mx = 0.0;
+    if (live)
+        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(oz_load(X, r, k)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    bool bad = false;
+    if (live)   // a non-finite entry makes the row's slices non-finite (fmax drops NaN)
+        for (int k = lane; k < K; k += 32) bad |= !isfinite(oz_load(X, r, k));
+    bad = __any_sync(0xffffffffu, bad);
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
+    if (lane == 0) ex[r] = e;
+    const int rt = r / kTileRows, rr = r % kTileRows;
+    const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
+    for (int g0 = lane * G; g0 < Kt * KT; g0 += 32 * G) {
+        double x[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int k = g0 + g;
+            x[g] = (live && k < K) ? oz_load(X, r, k) : 0.0;
+            if (bad && live && k < K) x[g] = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        uint4 sl[kS];
+        slice_group<G, kBf16>(x, e, sl);
+        const int kt = g0 / KT, kk = g0 % KT;
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * kBlock;
+            *reinterpret_cast<uint4*>(blk + within + (size_t)(kk / G) * LBO) = sl[t];
+        }
+    }
+}
+
+template <bool kBf16>
+__global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* probs,
+                                                               unsigned long long timeout_ns) {
+    constexpr int esize = kBf16 ? 2 : 4;
+    constexpr int KT = kt_elems(esize);
+    constexpr int kRangeTiles = kRangeK / KT;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const OzProblem& P = probs[blockIdx.z];
+    const int N = P.Ndyn ? *P.Ndyn : P.N;
+    const int mt = blockIdx.y, nt = blockIdx.x;
+    if (mt * kTileRows >= P.M || nt * kTileRows >= N) return;
+    const int Kt = P.Kt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+    // bar[0..1] full, bar[2..3] empty, bar[4] acc full, bar[5] acc empty, bar[6] final
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes + 64);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kStages * kStageBytes + 80);
+    if (threadIdx.x == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + s)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 2 + s)));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 4)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(bar + 5)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 6)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const int nrange = (Kt + kRangeTiles - 1) / kRangeTiles;
+
+    if (warp == 0) {
+        // producer: bulk copies of the slice blocks of k tile kt into stage kt % 2
+        if (lane == 0) {
+            const unsigned char* as = static_cast<const unsigned char*>(P.as);
+            const unsigned char* bs = static_cast<const unsigned char*>(P.bs);
+            int issued = 0;
+            for (int kt = 0; kt < Kt; ++kt) {
+                const int s = kt % kStages;
+                if (kt >= kStages && !mbar_wait(smem_u32(bar + 2 + s), ((kt / kStages) - 1) & 1, abort_flag, timeout_ns))
+                    break;
+                const uint32_t full = smem_u32(bar + s);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(kStageBytes)
+                             : "memory");
+                unsigned char* st = smem + (size_t)s * kStageBytes;
+                for (int t = 0; t < kS; ++t) {
+                    const unsigned char* srcA = as + (((size_t)t * P.Mt + mt) * Kt + kt) * kBlock;
+                    const unsigned char* srcB = bs + (((size_t)t * P.Nt + nt) * Kt + kt) * kBlock;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(st + t * kBlock)),
+                        "l"(srcA), "r"(kBlock), "r"(full)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(st + (kS + t) * kBlock)),
+                        "l"(srcB), "r"(kBlock), "r"(full)
+                        : "memory");
+                }
+                issued = kt + 1;
+            }
+            // copies still in flight complete on their full barrier before the CTA leaves
+            for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
+                mbar_wait(smem_u32(bar + kt % kStages), (kt / kStages) & 1, abort_flag, timeout_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = idesc(kBf16, kTileRows, kTileRows);
+            int r = 0;
+            bool first[kLevels] = {true, true, true, true};
+            int committed_final = 0;
+            for (int kt = 0; kt < Kt; ++kt) {
+                const int s = kt % kStages;
+                if (kt % kRangeTiles == 0 && kt > 0) {
+                    // accumulators of the previous range must be drained first
+                    if (!mbar_wait(smem_u32(bar + 5), (r - 1) & 1, abort_flag, timeout_ns)) break;
+                    first[0] = first[1] = first[2] = first[3] = true;
+                }
+                if (!mbar_wait(smem_u32(bar + s), (kt / kStages) & 1, abort_flag, timeout_ns)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
+#pragma unroll
+                for (int p = 0; p < kPairs; ++p) {
+                    const int t = pair_t(p), u = pair_u(p);
+                    const int lvl = (t + u) < kLevels - 1 ? (t + u) : kLevels - 1;
+                    const uint32_t d = tmem + (uint32_t)(lvl * kTileRows);
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        const uint32_t off = q * 2 * LBO;
+                        mma(kBf16, d, smem_desc(st + t * kBlock + off), smem_desc(st + (kS + u) * kBlock + off), id,
+                            first[lvl] ? 0u : 1u);
+                        first[lvl] = false;
+                    }
+                }
+                commit(smem_u32(bar + 2 + s));   // frees the stage once these MMAs have read it
+                if (kt % kRangeTiles == kRangeTiles - 1 || kt == Kt - 1) {
+                    commit(smem_u32(bar + 4));   // accumulators of range r complete
+                    ++r;
+                }
+                committed_final = kt + 1;
+            }
+            commit(smem_u32(bar + 6));
+            mbar_wait(smem_u32(bar + 6), 0, abort_flag, timeout_ns);   // every MMA issued has completed
+            (void)committed_final;
+        }
+    } else {
+        // epilogue warps 2..9: rows 32 (warp % 4) + lane, columns half * 64 .. + 63
+        const int ew = warp - 2;
+        const int lane_base = 32 * (warp & 3);
+        const int half = ew >> 2;
+        const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * 64);
+        double acc[64];
+#pragma unroll
+        for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+        bool ok = true;
+        for (int r = 0; r < nrange; ++r) {
+            if (!mbar_wait(smem_u32(bar + 4), r & 1, abort_flag, timeout_ns)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int lvl = 0; lvl < kLevels; ++lvl) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float v[16];
+                    tmem_ld16(taddr + (uint32_t)(lvl * kTileRows + c * 16), v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[c * 16 + i] += (double)v[i];
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + 5)) : "memory");
+        }
+        if (ok && !*abort_flag) {
+            const int i = mt * kTileRows + lane_base + lane;
+            if (i < P.M) {
+                const int ei = P.ea[i];
+#pragma unroll
+                for (int jj = 0; jj < 64; ++jj) {
+                    const int j = nt * kTileRows + half * 64 + jj;
+                    if (j >= N) continue;
+                    double v = P.alpha * ldexp(acc[jj], ei + P.eb[j] - 14);
+                    if (P.D) {
+                        const size_t di = (size_t)i * P.ldd + j;
+                        v += P.beta * (P.d_f32 ? (double)static_cast<const float*>(P.D)[di]
+                                               : static_cast<const double*>(P.D)[di]);
+                    }
+                    if (P.sub_identity && i == j) v -= 1.0;
+                    const size_t ci = (size_t)i * P.ldc + j;
+                    if (P.c_f32)
+                        static_cast<float*>(P.C)[ci] = (float)v;
+                    else
+                        static_cast<double*>(P.C)[ci] = v;
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+    if (threadIdx.x == 0 && *abort_flag && P.status) atomicOr(P.status, (int)MPDO_ST_TIMEOUT);
+}
+
+// The problems of one kind for every op of a chunk, from the op descriptors.
+__global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProblem* out, int cap, int bf16) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nops) return;
+    const OpDesc& d = descs[s];
+    const int ld = 4 * cap;
+    OzProblem P{};
+    auto rowmajor = [](const void* base, int f32, long long ld_) {   // (r, k) at r * ld + k
+        return OzOperand{base, f32, ld_, 1, 0, 1, 1};
+    };
+    auto colmajor = [](const void* base, int f32, long long ld_) {   // (r, k) at k * ld + r
+        return OzOperand{base, f32, 1, ld_, 0, 1, 1};
+    };
+    switch (kind) {
+        case OZ_MERGE:   // Theta[(l, s1), (s2, r)] = sum_m A[(l, s1), m] B[m, (s2, r)]
+            P.M = 4 * d.cl;
+            P.K = d.cm;
+            P.N = 4 * d.cr;
+            P.A = rowmajor(d.A, d.site_f32, cap);
+            P.B = OzOperand{d.B, d.site_f32, 0, 0, 1, d.cr, cap};
+            P.C = d.thetap;
+            P.ldc = ld;
+            break;
+        case OZ_RECON:   // B_p'[(l, s1), j] = sum_c Theta'[(l, s1), c] Yk[j, c], j < k (device)
+            P.M = d.m;
+            P.K = d.n;
+            P.N = min(d.chi_max, d.c);
+            P.Ndyn = d.k_out;
+            P.A = rowmajor(d.thetap, 0, ld);
+            P.B = rowmajor(d.Yk, 0, ld);
+            P.C = d.A;
+            P.ldc = cap;
+            P.c_f32 = d.site_f32;
+            break;
+        case OZ_E:       // E = U U^T - I
+            P.M = P.N = P.K = d.c;
+            P.A = rowmajor(d.U32, 1, ld);
+            P.B = rowmajor(d.U32, 1, ld);
+            P.C = d.E;
+            P.ldc = ld;
+            P.sub_identity = 1;
+            break;
+        case OZ_Q:       // Q = U - E U / 2
+            P.M = P.N = P.K = d.c;
+            P.A = rowmajor(d.E, 0, ld);
+            P.B = colmajor(d.U32, 1, ld);
+            P.C = d.Q;
+            P.ldc = ld;
+            P.alpha = -0.5;
+            P.beta = 1.0;
+            P.D = d.U32;
+            P.ldd = ld;
+            P.d_f32 = 1;
+            break;
+        default:         // OZ_W: W = Q W0
+            P.M = d.c;
+            P.N = d.L;
+            P.K = d.c;
+            P.A = rowmajor(d.Q, 0, ld);
+            P.B = colmajor(d.W0, 0, ld);
+            P.C = d.W;
+            P.ldc = ld;
+            break;
+    }
+    if (kind != OZ_Q) {
+        P.alpha = 1.0;
+        P.beta = 0.0;
+    }
+    P.as = d.oz_as;
+    P.bs = d.oz_bs;
+    P.ea = d.oz_ea;
+    P.eb = d.oz_eb;
+    P.status = d.status;
+    const int KT = kt_elems(bf16 ? 2 : 4);
+    P.Mt = (P.M + kTileRows - 1) / kTileRows;
+    P.Nt = (P.N + kTileRows - 1) / kTileRows;
+    P.Kt = (P.K + KT - 1) / KT;
+    out[s] = P;
+}
+
+// Theta' = G Theta in place (rows (l, s1), columns s2 cr + r) and theta~ =
+// lambda_{p-1}[l] Theta' column-major in Acm; one thread per (l, r).
+__global__ void __launch_bounds__(256) gate_weight_kernel(const OpDesc* descs, int chi_cap) {
+    const OpDesc& d = descs[blockIdx.y];
+    __shared__ double Gs[256];
+    Gs[threadIdx.x] = d.G[threadIdx.x];
+    __syncthreads();
+    const int ld = 4 * chi_cap;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= d.cl * d.cr) return;
+    const int l = e / d.cr, r = e % d.cr;
+    double th[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) th[i] = d.thetap[(size_t)(l * 4 + (i >> 2)) * ld + (i & 3) * d.cr + r];
+    const double lam = d.lam_left ? d.lam_left[l] : 1.0;
+#pragma unroll 4
+    for (int o = 0; o < 16; ++o) {
+        double v = 0.0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v = fma(Gs[o * 16 + i], th[i], v);
+        const int row = l * 4 + (o >> 2), col = (o & 3) * d.cr + r;
+        d.thetap[(size_t)row * ld + col] = v;
+        d.Acm[(size_t)col * ld + row] = lam * v;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* probs, int chi_cap, bool bf16,
+                          unsigned long long timeout_ns, cudaStream_t st) {
+    if (nops <= 0) return cudaSuccess;
+    oz_prep_kernel<<<(nops + 127) / 128, 128, 0, st>>>(d_desc, nops, kind, probs, chi_cap, bf16 ? 1 : 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int big = 4 * chi_cap;
+    return launch_oz_gemm(probs, nops, big, big, big, bf16, timeout_ns, st);
+}
+
+cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st) {
+    if (nops <= 0) return cudaSuccess;
+    dim3 g((chi_cap * chi_cap + 255) / 256, nops);
+    gate_weight_kernel<<<g, 256, 0, st>>>(d_desc, chi_cap);
+    return cudaGetLastError();
+}
+
+size_t oz_slice_bytes(int rows, int K, bool bf16) {
+    const int KT = kt_elems(bf16 ? 2 : 4);
+    const size_t Rt = (rows + kTileRows - 1) / kTileRows, Kt = (K + KT - 1) / KT;
+    return (size_t)kS * Rt * Kt * kBlock;
+}
+
+void oz_tiles(OzProblem& p, bool bf16) {
+    const int KT = kt_elems(bf16 ? 2 : 4);
+    p.Mt = (p.M + kTileRows - 1) / kTileRows;
+    p.Nt = (p.N + kTileRows - 1) / kTileRows;
+    p.Kt = (p.K + KT - 1) / KT;
+}
+
+cudaError_t oz_prepare() {
+    cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(oz_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+}
+
+cudaError_t launch_oz_gemm(const OzProblem* d_probs, int count, int max_m, int max_n, int max_rows_sliced,
+                           bool bf16, unsigned long long timeout_ns, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int mt = (max_m + kTileRows - 1) / kTileRows, nt = (max_n + kTileRows - 1) / kTileRows;
+    const int rows = ((max_rows_sliced + kTileRows - 1) / kTileRows) * kTileRows;
+    dim3 sg((rows + 7) / 8, 2, count);
+    if (bf16)
+        oz_slice_kernel<true><<<sg, 256, 0, st>>>(d_probs);
+    else
+        oz_slice_kernel<false><<<sg, 256, 0, st>>>(d_probs);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 g(nt, mt, count);
+    if (bf16)
+        oz_gemm_kernel<true><<<g, kThreads, kSmem, st>>>(d_probs, timeout_ns);
+    else
+        oz_gemm_kernel<false><<<g, kThreads, kSmem, st>>>(d_probs, timeout_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace mpdo
+
+// ---------------------------------------------------------------------------
+// mpdo_gemm_tc: the same product on caller matrices (include/mpdo.h)
+// ---------------------------------------------------------------------------
+#include <string>
+
+extern "C" int mpdo_gemm_tc(int M, int N, int K, const double* A, int lda, const double* B, int ldb, double* C,
+                            int ldc, int kind, void* cuda_stream) {
+    using namespace mpdo;
+    if (M < 1 || N < 1 || K < 1 || lda < K || ldb < N || ldc < N || !A || !B || !C) {
+        set_last_error("mpdo_gemm_tc: need M, N, K >= 1, lda >= K, ldb >= N, ldc >= N and non-NULL matrices");
+        return MPDO_EINVAL;
+    }
+    if (kind != MPDO_MIXED_TF32 && kind != MPDO_MIXED_BF16X3) {
+        set_last_error("mpdo_gemm_tc: kind must be MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
+        return MPDO_EINVAL;
+    }
+    const bool bf16 = kind == MPDO_MIXED_BF16X3;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    OzProblem P{};
+    P.M = M;
+    P.N = N;
+    P.K = K;
+    P.A = OzOperand{A, 0, lda, 1, 0, 1, 1};
+    P.B = OzOperand{B, 0, 1, ldb, 0, 1, 1};
+    P.C = C;
+    P.ldc = ldc;
+    P.alpha = 1.0;
+    oz_tiles(P, bf16);
+    const size_t sa = oz_slice_bytes(M, K, bf16), sb = oz_slice_bytes(N, K, bf16);
+    unsigned char* buf = nullptr;
+    const size_t ia = (size_t)P.Mt * 128, ib = (size_t)P.Nt * 128;
+    const size_t bytes = sa + sb + sizeof(int) * (ia + ib) + sizeof(OzProblem) + 256;
+    cudaError_t e = cudaMalloc((void**)&buf, bytes);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("mpdo_gemm_tc: ") + cudaGetErrorString(e));
+        return MPDO_ENOMEM;
+    }
+    P.as = buf;
+    P.bs = buf + sa;
+    P.ea = reinterpret_cast<int*>(buf + sa + sb);
+    P.eb = P.ea + ia;
+    OzProblem* d_p = reinterpret_cast<OzProblem*>(
+        (reinterpret_cast<uintptr_t>(P.eb + ib) + 255) & ~static_cast<uintptr_t>(255));
+    e = oz_prepare();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_p, &P, sizeof(P), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_oz_gemm(d_p, 1, M, N, M > N ? M : N, bf16, 4000000000ull, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(buf);
+    if (e != cudaSuccess) {
+        set_last_error(std::string("mpdo_gemm_tc: ") + cudaGetErrorString(e));
+        return MPDO_ECUDA;
+    }
+    return MPDO_OK;
+}

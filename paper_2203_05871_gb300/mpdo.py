@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
         "mpdo_inject_fault": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_renyi2": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "mpdo_gemm_tc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
+                                        vp, ctypes.c_int, ctypes.c_int, vp]),
         "mpdo_osee": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
         "mpdo_autotune": (ctypes.c_int, [vp, _ip, ctypes.c_int, _ip]),
         "mpdo_grad_forward": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -113,7 +115,7 @@ def exported_symbols() -> list[str]:
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
-            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_renyi2", "mpdo_osee", "mpdo_grad_forward",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_renyi2", "mpdo_osee", "mpdo_gemm_tc", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -140,6 +142,22 @@ def schedule(n: int, bonds):
             layers.append([])
         layers[li].append(("swap" if kind else "gate", p, qa, qb, bond, f2 / 2.0))
     return layers
+
+
+def gemm_tc(A, B, kind: int = MIXED_TF32, stream=None):
+    """C = A B (CUDA float64 torch tensors, row-major) by the library's
+    FP64-accurate tensor-core GEMM (mpdo_gemm_tc); returns C."""
+    import torch
+    lib = load_library()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2 and A.dtype == torch.float64 and B.dtype == torch.float64
+    A, B = A.contiguous(), B.contiguous()
+    C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+    st = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+    _check(lib.mpdo_gemm_tc(M, N, K, ctypes.c_void_p(A.data_ptr()), K, ctypes.c_void_p(B.data_ptr()), N,
+                            ctypes.c_void_p(C.data_ptr()), N, int(kind), st))
+    return C
 
 
 def _check(code):

@@ -201,22 +201,25 @@ def test_chi256_one_step_sampled():
 # ---------------------------------------------------------------------------
 # mixed-precision path: FP32 preconditioning Jacobi + FP64 finishing sweeps
 # ---------------------------------------------------------------------------
-def _mixed():
-    from paper_2203_05871_gb300 import MIXED_TF32
-    return MIXED_TF32
+def _mixed(kind="tf32"):
+    from paper_2203_05871_gb300 import MIXED_BF16X3, MIXED_TF32
+    return MIXED_TF32 if kind == "tf32" else MIXED_BF16X3
 
 
-def test_mixed_chain8_forty_steps():
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
+def test_mixed_chain8_forty_steps(kind):
     wl = W.chain8_fp64()
-    s = solver_for(wl, precision=_mixed())
+    s = solver_for(wl, precision=_mixed(kind))
     worst = compare_to_oracle(wl, wl.steps, s, tol=TOL_MIXED)
+    print(f"mixed {kind} chain8 x 40 steps: worst |d| = {worst:.2e}")
     assert worst <= TOL_MIXED
 
 
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
 @pytest.mark.parametrize("bonds,n", [(W.ring_bonds(8), 8), (W.grid_snake_bonds(3, 3), 9)])
-def test_mixed_swap_routed(bonds, n):
+def test_mixed_swap_routed(bonds, n, kind):
     wl = W.random_model(n, bonds, 57, chi_max=32, cutoff=1e-11, dt=0.05)
-    s = solver_for(wl, precision=_mixed())
+    s = solver_for(wl, precision=_mixed(kind))
     compare_to_oracle(wl, 3, s, tol=TOL_MIXED)
 
 
@@ -227,18 +230,18 @@ def test_mixed_batched_uneven_chi():
     compare_to_oracle(wl, 4, s, tol=TOL_MIXED)
 
 
-# decay 0.045: a graded spectrum like the physical workloads', held to the
-# mixed tolerance.  decay 0: a flat random spectrum cut from 1024 values to
-# 256, where the gap at the cut is tiny and the kept subspace turns by
-# (perturbation / gap): FP32-level contraction errors grow far past 1e-5
-# there, so that input is only held to 1e-3 (the FP64 test above holds it to
-# 1e-10).
-@pytest.mark.parametrize("decay,tol", [(0.0, 1e-3), (0.045, TOL_MIXED)])
-def test_mixed_chi256_one_step_sampled(decay, tol):
+# decay 0.045: a graded spectrum like the physical workloads'.  decay 0: a flat
+# random spectrum cut from 1024 values to 256, where the gap at the cut is tiny
+# and the kept subspace turns by (perturbation / gap): the contractions and the
+# preconditioner products must be FP64-class (the tensor-core slice products
+# are) for the mixed tolerance to hold there.
+@pytest.mark.parametrize("kind", ["tf32", "bf16"])
+@pytest.mark.parametrize("decay,tol", [(0.0, TOL_MIXED), (0.045, TOL_MIXED)])
+def test_mixed_chi256_one_step_sampled(decay, tol, kind):
     n = 10
     wl = W.uniform_model("chain10_chi256", n, W.chain_bonds(n), chi_max=256, cutoff=1e-10, dt=0.02)
     dims, tens = W.random_mpo_state(n, 256, seed=11, decay=decay)
-    s = solver_for(wl, chi_cap=256, precision=_mixed())
+    s = solver_for(wl, chi_cap=256, precision=_mixed(kind))
     s.set_state(0, dims, tens)
     s.step(1)
     log = [int(k) for k in s.rank_log(1)[0]]
@@ -248,12 +251,14 @@ def test_mixed_chi256_one_step_sampled(decay, tol):
     # a random MPO is not a physical density matrix: its "expectation values"
     # are ratios of small traces and can exceed 1, so the bound is relative
     gz, rz = s.measure_1q(range(n), "Z")[0], o.z()
-    assert np.all(np.abs(gz - rz) <= tol * np.maximum(1.0, np.abs(rz)))
     pairs = [(0, 9), (3, 6), (4, 5), (1, 8)]
     # connected values are differences of terms that can be large here: bound by their size
     g, rg = s.measure_2q(pairs, "ZZ", connected=True)[0], o.zz_connected(pairs)
     scale = np.array([abs(o.state.expect_2q(i, j)) + abs(rz[i] * rz[j]) for (i, j) in pairs])
-    assert np.all(np.abs(g - rg) <= tol * np.maximum(1.0, scale))
+    ez = np.abs(gz - rz) / np.maximum(1.0, np.abs(rz))
+    ezz = np.abs(g - rg) / np.maximum(1.0, scale)
+    print(f"mixed {kind} chi256 decay {decay}: max rel |dZ| = {ez.max():.2e}, |dZZc| = {ezz.max():.2e}")
+    assert np.all(ez <= tol) and np.all(ezz <= tol)
     md = s.status()["max_discarded"][0]
     assert o.max_discarded > 0.0 and abs(md - o.max_discarded) <= tol * o.max_discarded
 
