@@ -100,10 +100,10 @@ def pauli_expect(r, n, comps):
 class DenseTrotter:
     """Op list of ``schedule.step_layers`` applied to the 4^N vector."""
 
-    def __init__(self, wl, b=0, r0=None):
+    def __init__(self, wl, b=0, r0=None, order=2):
         self.wl = wl
         self.n = wl.n
-        self.layers = schedule.step_layers(wl.n, wl.bonds)
+        self.layers = schedule.step_layers_order(wl.n, wl.bonds, order)
         self.gates = tebd.build_gates(wl, b, self.layers, wl.dt)
         if r0 is None:
             st = tebd.MPOState(*tebd.product_state(wl.n, wl.init))

@@ -19,6 +19,13 @@ two-site-gate schedule; this module takes the following reading:
 An op is the tuple (kind, p, qa, qb, bond, frac): kind 'gate' or 'swap', left
 path position p, qubits qa at p and qb at p+1 before the op, bond index (-1 for
 swaps) and the fraction of dt (0 for swaps).
+
+Fourth order (the paper uses order 4 throughout, App. B; its W^II MPO is not
+the blueprint here): Suzuki's symmetric triple jump of the second-order step,
+S4(dt) = S2(w1 dt) S2(w0 dt) S2(w1 dt) with w1 = 1 / (2 - 2^(1/3)) and
+w0 = 1 - 2 w1 (negative), i.e. the three op lists one after the other with
+their gate fractions scaled.  Symmetric compositions have even order, so no
+third-order variant is built.
 """
 from __future__ import annotations
 
@@ -114,3 +121,22 @@ def count_ops(layers):
     g = sum(1 for L in layers for o in L if o[0] == "gate")
     s = sum(1 for L in layers for o in L if o[0] == "swap")
     return g, s
+
+
+W1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+W0 = 1.0 - 2.0 * W1
+
+
+def step_layers_order(n: int, bonds: Sequence[Tuple[int, int]], order: int = 2) -> List[List[Op]]:
+    """Layers of one step of Trotter order 2 or 4 (module docstring)."""
+    S = step_layers(n, bonds)
+    if order == 2:
+        return S
+    if order != 4:
+        raise ValueError("Trotter order must be 2 or 4")
+    out = []
+    for w in (W1, W0, W1):
+        for layer in S:
+            out.append([(kind, p, qa, qb, k, frac * w if kind == "gate" else frac)
+                        for (kind, p, qa, qb, k, frac) in layer])
+    return out

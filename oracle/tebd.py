@@ -181,10 +181,10 @@ def build_gates(wl, b, layers, dt):
 class TEBD:
     """Plain sequential MPO-TEBD for instance ``b`` of a workload."""
 
-    def __init__(self, wl, b=0, state: Optional[MPOState] = None, force_trace=True, tol=None):
+    def __init__(self, wl, b=0, state: Optional[MPOState] = None, force_trace=True, tol=None, order=2):
         self.wl = wl
         self.b = b
-        self.layers = schedule.step_layers(wl.n, wl.bonds)
+        self.layers = schedule.step_layers_order(wl.n, wl.bonds, order)
         self.gates = build_gates(wl, b, self.layers, wl.dt)
         self.chi_max = int(wl.chi_max[b])
         self.cutoff = float(wl.cutoff[b])
