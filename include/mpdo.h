@@ -72,7 +72,9 @@ typedef struct {
                                 and the measurements still compute in FP64 or the chosen
                                 mixed precision, and round the new sites to float).  The
                                 gradient needs MPDO_STORE_F64. */
-    int trotter_order;       /* 2 (symmetric second-order product) */
+    int trotter_order;       /* 2: symmetric second-order product; 4: Suzuki's triple jump
+                                S2(w1 dt) S2(w0 dt) S2(w1 dt), w1 = 1/(2 - 2^(1/3)), w0 = 1 - 2 w1
+                                (App. B uses order 4; odd orders are not built) */
     int force_trace;         /* 1: rho /= tr rho after every step (App. B b_force_rho_trace) */
     int jacobi_max_sweeps;   /* sweep limit of the Jacobi SVD (default 100, at most 128) */
     double jacobi_tol;       /* <= 0: sqrt(L) * DBL_EPSILON for rows of length L */
@@ -110,7 +112,7 @@ int mpdo_init(mpdo_ctx **out, const mpdo_config *cfg, void *cuda_stream);
  * chi_max > chi_cap, malformed init string), ECUDA. */
 int mpdo_build_gates(mpdo_ctx *ctx, const mpdo_model *model, double dt);
 
-/* Advance every instance by n_steps second-order Trotter steps.  Per op:
+/* Advance every instance by n_steps Trotter steps (cfg.trotter_order).  Per op:
  * merge the two sites, apply the gate, weight by the left Schmidt values,
  * Householder QR (only R is kept), SVD of R (FP64 one-sided Jacobi on its
  * rows), truncate, write the two new sites.  After each

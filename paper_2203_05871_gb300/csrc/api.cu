@@ -103,7 +103,7 @@ int alloc_slots(mpdo_ctx* c, int want) {
     if (c->mixed) {
         c->oz_slot_bytes = oz_slice_bytes(c->ld, c->ld, c->oz_bf16);
         per_slot_bytes += 3 * mat * sizeof(double) + 2 * mat * sizeof(float) + 2 * c->oz_slot_bytes +
-                          2 * (size_t)c->ld * sizeof(int);
+                          2 * oz_exp_ints(c->ld) * sizeof(int);
     }
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
@@ -137,8 +137,8 @@ int alloc_slots(mpdo_ctx* c, int want) {
         CU(dalloc(&c->d_U32, (size_t)s * mat));
         CU(dalloc(&c->d_oz_as, (size_t)s * c->oz_slot_bytes));
         CU(dalloc(&c->d_oz_bs, (size_t)s * c->oz_slot_bytes));
-        CU(dalloc(&c->d_oz_ea, (size_t)s * c->ld));
-        CU(dalloc(&c->d_oz_eb, (size_t)s * c->ld));
+        CU(dalloc(&c->d_oz_ea, (size_t)s * oz_exp_ints(c->ld)));
+        CU(dalloc(&c->d_oz_eb, (size_t)s * oz_exp_ints(c->ld)));
         CU(dalloc(&c->d_oz, (size_t)s));
     }
     return MPDO_OK;
@@ -276,8 +276,8 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.Zinit = nullptr;
     d.oz_as = c->mixed ? c->d_oz_as + (size_t)s * c->oz_slot_bytes : nullptr;
     d.oz_bs = c->mixed ? c->d_oz_bs + (size_t)s * c->oz_slot_bytes : nullptr;
-    d.oz_ea = c->mixed ? c->d_oz_ea + (size_t)s * ld : nullptr;
-    d.oz_eb = c->mixed ? c->d_oz_eb + (size_t)s * ld : nullptr;
+    d.oz_ea = c->mixed ? c->d_oz_ea + (size_t)s * oz_exp_ints(ld) : nullptr;
+    d.oz_eb = c->mixed ? c->d_oz_eb + (size_t)s * oz_exp_ints(ld) : nullptr;
 }
 
 int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,
@@ -591,7 +591,8 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
         return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");
     if (cfg->storage != MPDO_STORE_F64 && cfg->storage != MPDO_STORE_F32)
         return fail(MPDO_EINVAL, "storage must be MPDO_STORE_F64 or MPDO_STORE_F32");
-    if (cfg->trotter_order != 2) return fail(MPDO_EINVAL, "trotter_order must be 2");
+    if (cfg->trotter_order != 2 && cfg->trotter_order != 4)
+        return fail(MPDO_EINVAL, "trotter_order must be 2 or 4 (symmetric compositions have even order)");
     if (cfg->jacobi_max_sweeps < 1 || cfg->jacobi_max_sweeps > kMaxSweepsCap)
         return fail(MPDO_EINVAL, "jacobi_max_sweeps must be in [1, 128]");
     if (cfg->barrier_timeout_ms < 1) return fail(MPDO_EINVAL, "barrier_timeout_ms must be >= 1");
@@ -669,6 +670,17 @@ int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
     std::vector<double> weights;
     std::string err = build_schedule(N, bi, bj, layers, weights);
     if (!err.empty()) return fail(MPDO_EINVAL, "bond graph: " + err);
+    if (c->cfg.trotter_order == 4) {
+        // Suzuki's symmetric triple jump: S2(w1 dt) S2(w0 dt) S2(w1 dt), w0 + 2 w1 = 1
+        const double w1 = 1.0 / (2.0 - std::cbrt(2.0)), w0 = 1.0 - 2.0 * w1;
+        std::vector<Layer> four;
+        for (double w : {w1, w0, w1})
+            for (Layer L : layers) {
+                for (auto& o : L) o.frac *= w;
+                four.push_back(L);
+            }
+        layers.swap(four);
+    }
     c->layers = layers;
     c->weights = weights;
     c->nb = nb;

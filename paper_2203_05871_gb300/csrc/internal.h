@@ -182,10 +182,11 @@ struct OzProblem {
     int ldd, d_f32, sub_identity;
     void *as, *bs;       // slice blocks of A and B
     int *ea, *eb;        // row / column exponents
-    int Mt, Nt, Kt;      // tiles (128 rows, 128 columns, 64 bytes of K)
+    int Mt, Nt, Kt;      // tiles (128 rows, 64 columns, 64 bytes of K)
     int* status;         // MPDO_ST_TIMEOUT when a wait gives up (or nullptr)
 };
-size_t oz_slice_bytes(int rows, int K, bool bf16);
+size_t oz_slice_bytes(int rows, int K, bool bf16);   // slice blocks of an operand of rows x K
+size_t oz_exp_ints(int rows);                          // its exponent array (rows rounded up to a tile)
 void oz_tiles(OzProblem& p, bool bf16);
 cudaError_t oz_prepare();
 // slices both operands of count problems, then multiplies; max_m / max_n /

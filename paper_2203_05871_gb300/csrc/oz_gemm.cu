@@ -18,31 +18,35 @@
 // 2. Products (oz_gemm_kernel).  Every slice pair (t, u) with t + u <= 5 is
 //    multiplied on the tensor core: a product sigma_t sigma_u has at most 16
 //    bits, so it is exact in FP32, and the sums stay exact while they fit 24
-//    bits.  Four accumulators in tensor memory, each product already at its
-//    own scale 2^-8(t+u) through the stored slices: level 0 (pair (0,0)),
-//    level 1 ((0,1), (1,0)), level 2 (three pairs) and level 3+ (the fifteen
-//    pairs of levels 3-5).  Every 256 values of K the accumulators are drained
-//    into FP64 registers: 256 products of up to 2^14 fit 2^22, so levels 0, 1
-//    and 2 (at most three pairs) are summed without any rounding; level 3+
-//    rounds at 2^-24 of itself, about 2^-46 of the result.
-// 3. Epilogue: C_ij = alpha 2^(e_i + f_j - 14) (L0 + L1 + L2 + L3) + beta D_ij.
+//    bits.  One accumulator per level d = t + u in tensor memory (six), each
+//    product already at its own scale 2^-8d through the stored slices.  Every
+//    256 values of K the accumulators are drained into FP64 registers: 256
+//    products of up to 2^14 fit 2^22, so levels 0 to 3 (at most four pairs,
+//    2^24) are summed without any rounding, whatever rounding and alignment
+//    the tensor core's FP32 accumulation uses; levels 4 and 5 round at 2^-24
+//    of themselves, below 2^-50 of the result.  (Folding levels 3-5 into one
+//    accumulator was measured at 2e-12 on the GPU: the accumulator then holds
+//    level-3 magnitudes and drops the low bits of every level-5 product at
+//    every MMA.)
+// 3. Epilogue: C_ij = alpha 2^(e_i + f_j - 14) sum_d L_d + beta D_ij.
 // Error: about 2^-46 |A_i|_max |B_j|_max per term of the sum (a numpy model of
-// the scheme: 6e-14 normwise on 1024 x 1024 x 1024, graded or not), against
+// the scheme with per-MMA rounding: 3e-14 of |A_i| |B_j| sqrt(K)), against
 // FP64's 2^-53 |A_ik B_kj|: FP64-class accuracy at tensor-core speed.
 //
 // Data layout.  The slices are written in the tcgen05 canonical K-major,
-// no-swizzle layout, pre-tiled: a block of 128 rows x 64 bytes of K (32 bf16 or
-// 16 tf32 values) is 8 KB, element (row, k) at (row/8)*512 + (k/g)*128 +
-// (row%8)*16 + (k%g)*esize, g = 16/esize (core matrices of 8 rows x 16 bytes,
-// LBO = 128 B along K, SBO = 512 B along rows), so one cp.async.bulk moves a
-// block into shared memory as it is.  Blocks are [slice][row tile][k tile].
+// no-swizzle layout, pre-tiled: a block of R rows x 64 bytes of K (32 bf16 or
+// 16 tf32 values; R = 128 for A, 64 for B) is R x 64 bytes, element (row, k) at
+// (row/8)*512 + (k/g)*128 + (row%8)*16 + (k%g)*esize, g = 16/esize (core
+// matrices of 8 rows x 16 bytes, LBO = 128 B along K, SBO = 512 B along rows),
+// so one cp.async.bulk moves a block into shared memory as it is.  Blocks are
+// [slice][row tile][k tile].
 //
-// Kernel.  One CTA per 128 x 128 tile of C, 320 threads: warp 0 issues the
-// bulk copies of the 6 + 6 slice blocks of each k tile into a 2-stage ring
-// (96 KB per stage), warp 1 issues the 42 MMAs of a k tile (21 pairs x 2
-// instructions of K = 16 bf16 / 8 tf32; M = 128, N = 128) and commits, warps
-// 2-9 drain the accumulators (warp w reads TMEM lanes 32 (w % 4) .. +31, its
-// half of the 128 columns).  Every wait is bounded by timeout_ns; a wait that
+// Kernel.  One CTA per 128 x 64 tile of C, 320 threads: warp 0 issues the
+// bulk copies of the 6 + 6 slice blocks of each k tile into a 3-stage ring
+// (72 KB per stage), warp 1 issues the 42 MMAs of a k tile (21 pairs x 2
+// instructions of K = 16 bf16 / 8 tf32; M = 128, N = 64) and commits, warps
+// 2-9 drain the six accumulators (384 TMEM columns; warp w reads lanes
+// 32 (w % 4) .. +31, its half of the 64 columns).  Every wait is bounded by timeout_ns; a wait that
 // gives up records MPDO_ST_TIMEOUT in the problem's status word, the other roles
 // leave their loops at the next poll, outstanding copies and MMAs are waited
 // for (bounded) and the tensor memory is released before the CTA returns.
@@ -58,14 +62,17 @@ namespace {
 
 constexpr int kS = 6;                  // slices per operand
 constexpr int kPairs = 21;             // (t, u) with t + u <= 5
-constexpr int kLevels = 4;             // accumulators: levels 0, 1, 2 and 3+
-constexpr int kBlock = 8192;           // bytes of one 128-row x 64-byte slice block
-constexpr int kTileRows = 128;
-constexpr int kStageBytes = 2 * kS * kBlock;   // A and B slices of one k tile
-constexpr int kStages = 2;
+constexpr int kLevels = 6;             // one accumulator per level t + u
+constexpr int kTileM = 128;            // rows of A (and of C) per tile
+constexpr int kTileN = 64;             // columns of B (and of C) per tile
+constexpr int kBlockA = kTileM * 64;   // bytes of one slice block of A (8 KB)
+constexpr int kBlockB = kTileN * 64;   // of B (4 KB)
+constexpr int kStageBytes = kS * (kBlockA + kBlockB);   // A and B slices of one k tile
+constexpr int kStages = 3;
 constexpr int kRangeK = 256;           // K values between accumulator drains
 constexpr int kThreads = 320;
 constexpr int kSmem = kStages * kStageBytes + 1024;
+static_assert(kLevels * kTileN <= 512, "accumulators exceed tensor memory");
 constexpr int LBO = 128, SBO = 512;
 
 __host__ __device__ constexpr int kt_elems(int esize) { return 64 / esize; }
@@ -209,11 +216,12 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     const OzOperand& X = isB ? P.B : P.A;
     const int N = P.Ndyn ? *P.Ndyn : P.N;
     const int R = isB ? N : P.M;
+    const int tile = isB ? kTileN : kTileM;         // rows per block
     const int Rt = isB ? P.Nt : P.Mt;
     const int K = P.K, Kt = P.Kt;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = blockIdx.x * 8 + warp;
-    if (r >= Rt * kTileRows) return;
+    if (r >= Rt * tile) return;
     unsigned char* out = static_cast<unsigned char*>(isB ? P.bs : P.as);
     int* ex = isB ? P.eb : P.ea;
     const bool live = r < R;
@@ -229,7 +237,8 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     int e = 0;
     if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
     if (lane == 0) ex[r] = e;
-    const int rt = r / kTileRows, rr = r % kTileRows;
+    const int rt = r / tile, rr = r % tile;
+    const size_t block = (size_t)tile * 64;
     const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
     for (int g0 = lane * G; g0 < Kt * KT; g0 += 32 * G) {
         double x[G];
@@ -244,11 +253,15 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
         const int kt = g0 / KT, kk = g0 % KT;
 #pragma unroll
         for (int t = 0; t < kS; ++t) {
-            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * kBlock;
+            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * block;
             *reinterpret_cast<uint4*>(blk + within + (size_t)(kk / G) * LBO) = sl[t];
         }
     }
 }
+
+// barriers: full[kStages], empty[kStages], accumulators full, accumulators drained, final
+constexpr int kBarFull = 0, kBarEmpty = kStages, kBarAccFull = 2 * kStages, kBarAccEmpty = 2 * kStages + 1,
+              kBarFinal = 2 * kStages + 2;
 
 template <bool kBf16>
 __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* probs,
@@ -260,23 +273,22 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
     const OzProblem& P = probs[blockIdx.z];
     const int N = P.Ndyn ? *P.Ndyn : P.N;
     const int mt = blockIdx.y, nt = blockIdx.x;
-    if (mt * kTileRows >= P.M || nt * kTileRows >= N) return;
+    if (mt * kTileM >= P.M || nt * kTileN >= N) return;
     const int Kt = P.Kt;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-    // bar[0..1] full, bar[2..3] empty, bar[4] acc full, bar[5] acc empty, bar[6] final
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes + 64);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kStages * kStageBytes + 80);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kStages * kStageBytes + 128);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + kStages * kStageBytes + 144);
     if (threadIdx.x == 0) {
         *abort_flag = 0;
         for (int s = 0; s < kStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + s)));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 2 + s)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + kBarFull + s)));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + kBarEmpty + s)));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 4)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(bar + 5)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + 6)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + kBarAccFull)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(smem_u32(bar + kBarAccEmpty)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar + kBarFinal)));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     if (warp == 1) {
@@ -291,91 +303,92 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
     const int nrange = (Kt + kRangeTiles - 1) / kRangeTiles;
 
     if (warp == 0) {
-        // producer: bulk copies of the slice blocks of k tile kt into stage kt % 2
+        // producer: bulk copies of the slice blocks of k tile kt into stage kt % kStages
         if (lane == 0) {
             const unsigned char* as = static_cast<const unsigned char*>(P.as);
             const unsigned char* bs = static_cast<const unsigned char*>(P.bs);
             int issued = 0;
             for (int kt = 0; kt < Kt; ++kt) {
                 const int s = kt % kStages;
-                if (kt >= kStages && !mbar_wait(smem_u32(bar + 2 + s), ((kt / kStages) - 1) & 1, abort_flag, timeout_ns))
+                if (kt >= kStages &&
+                    !mbar_wait(smem_u32(bar + kBarEmpty + s), ((kt / kStages) - 1) & 1, abort_flag, timeout_ns))
                     break;
-                const uint32_t full = smem_u32(bar + s);
+                const uint32_t full = smem_u32(bar + kBarFull + s);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(full), "r"(kStageBytes)
                              : "memory");
                 unsigned char* st = smem + (size_t)s * kStageBytes;
                 for (int t = 0; t < kS; ++t) {
-                    const unsigned char* srcA = as + (((size_t)t * P.Mt + mt) * Kt + kt) * kBlock;
-                    const unsigned char* srcB = bs + (((size_t)t * P.Nt + nt) * Kt + kt) * kBlock;
+                    const unsigned char* srcA = as + (((size_t)t * P.Mt + mt) * Kt + kt) * kBlockA;
+                    const unsigned char* srcB = bs + (((size_t)t * P.Nt + nt) * Kt + kt) * kBlockB;
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(st + t * kBlock)),
-                        "l"(srcA), "r"(kBlock), "r"(full)
+                            smem_u32(st + t * kBlockA)),
+                        "l"(srcA), "r"(kBlockA), "r"(full)
                         : "memory");
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(st + (kS + t) * kBlock)),
-                        "l"(srcB), "r"(kBlock), "r"(full)
+                            smem_u32(st + kS * kBlockA + t * kBlockB)),
+                        "l"(srcB), "r"(kBlockB), "r"(full)
                         : "memory");
                 }
                 issued = kt + 1;
             }
             // copies still in flight complete on their full barrier before the CTA leaves
             for (int kt = (issued > kStages ? issued - kStages : 0); kt < issued; ++kt)
-                mbar_wait(smem_u32(bar + kt % kStages), (kt / kStages) & 1, abort_flag, timeout_ns);
+                mbar_wait(smem_u32(bar + kBarFull + kt % kStages), (kt / kStages) & 1, abort_flag, timeout_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id = idesc(kBf16, kTileRows, kTileRows);
+            const uint32_t id = idesc(kBf16, kTileM, kTileN);
             int r = 0;
-            bool first[kLevels] = {true, true, true, true};
-            int committed_final = 0;
+            bool first[kLevels];
+#pragma unroll
+            for (int l = 0; l < kLevels; ++l) first[l] = true;
             for (int kt = 0; kt < Kt; ++kt) {
                 const int s = kt % kStages;
                 if (kt % kRangeTiles == 0 && kt > 0) {
                     // accumulators of the previous range must be drained first
-                    if (!mbar_wait(smem_u32(bar + 5), (r - 1) & 1, abort_flag, timeout_ns)) break;
-                    first[0] = first[1] = first[2] = first[3] = true;
+                    if (!mbar_wait(smem_u32(bar + kBarAccEmpty), (r - 1) & 1, abort_flag, timeout_ns)) break;
+#pragma unroll
+                    for (int l = 0; l < kLevels; ++l) first[l] = true;
                 }
-                if (!mbar_wait(smem_u32(bar + s), (kt / kStages) & 1, abort_flag, timeout_ns)) break;
+                if (!mbar_wait(smem_u32(bar + kBarFull + s), (kt / kStages) & 1, abort_flag, timeout_ns)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t st = smem_u32(smem + (size_t)s * kStageBytes);
 #pragma unroll
                 for (int p = 0; p < kPairs; ++p) {
                     const int t = pair_t(p), u = pair_u(p);
-                    const int lvl = (t + u) < kLevels - 1 ? (t + u) : kLevels - 1;
-                    const uint32_t d = tmem + (uint32_t)(lvl * kTileRows);
+                    const int lvl = t + u;
+                    const uint32_t d = tmem + (uint32_t)(lvl * kTileN);
 #pragma unroll
                     for (int q = 0; q < 2; ++q) {
                         const uint32_t off = q * 2 * LBO;
-                        mma(kBf16, d, smem_desc(st + t * kBlock + off), smem_desc(st + (kS + u) * kBlock + off), id,
-                            first[lvl] ? 0u : 1u);
+                        mma(kBf16, d, smem_desc(st + t * kBlockA + off), smem_desc(st + kS * kBlockA + u * kBlockB + off),
+                            id, first[lvl] ? 0u : 1u);
                         first[lvl] = false;
                     }
                 }
-                commit(smem_u32(bar + 2 + s));   // frees the stage once these MMAs have read it
+                commit(smem_u32(bar + kBarEmpty + s));   // frees the stage once these MMAs have read it
                 if (kt % kRangeTiles == kRangeTiles - 1 || kt == Kt - 1) {
-                    commit(smem_u32(bar + 4));   // accumulators of range r complete
+                    commit(smem_u32(bar + kBarAccFull));   // accumulators of range r complete
                     ++r;
                 }
-                committed_final = kt + 1;
             }
-            commit(smem_u32(bar + 6));
-            mbar_wait(smem_u32(bar + 6), 0, abort_flag, timeout_ns);   // every MMA issued has completed
-            (void)committed_final;
+            commit(smem_u32(bar + kBarFinal));
+            mbar_wait(smem_u32(bar + kBarFinal), 0, abort_flag, timeout_ns);   // every MMA issued has completed
         }
     } else {
-        // epilogue warps 2..9: rows 32 (warp % 4) + lane, columns half * 64 .. + 63
+        // epilogue warps 2..9: rows 32 (warp % 4) + lane, columns half * 32 .. + 31
         const int ew = warp - 2;
         const int lane_base = 32 * (warp & 3);
         const int half = ew >> 2;
-        const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * 64);
-        double acc[64];
+        const uint32_t taddr = tmem + ((uint32_t)lane_base << 16) + (uint32_t)(half * 32);
+        double acc[32];
 #pragma unroll
-        for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+        for (int j = 0; j < 32; ++j) acc[j] = 0.0;
         bool ok = true;
         for (int r = 0; r < nrange; ++r) {
-            if (!mbar_wait(smem_u32(bar + 4), r & 1, abort_flag, timeout_ns)) {
+            if (!mbar_wait(smem_u32(bar + kBarAccFull), r & 1, abort_flag, timeout_ns)) {
                 ok = false;
                 break;
             }
@@ -383,9 +396,9 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
 #pragma unroll
             for (int lvl = 0; lvl < kLevels; ++lvl) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < 2; ++c) {
                     float v[16];
-                    tmem_ld16(taddr + (uint32_t)(lvl * kTileRows + c * 16), v);
+                    tmem_ld16(taddr + (uint32_t)(lvl * kTileN + c * 16), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int i = 0; i < 16; ++i) acc[c * 16 + i] += (double)v[i];
@@ -393,15 +406,16 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + 5)) : "memory");
+            if (lane == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar + kBarAccEmpty)) : "memory");
         }
         if (ok && !*abort_flag) {
-            const int i = mt * kTileRows + lane_base + lane;
+            const int i = mt * kTileM + lane_base + lane;
             if (i < P.M) {
                 const int ei = P.ea[i];
 #pragma unroll
-                for (int jj = 0; jj < 64; ++jj) {
-                    const int j = nt * kTileRows + half * 64 + jj;
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int j = nt * kTileN + half * 32 + jj;
                     if (j >= N) continue;
                     double v = P.alpha * ldexp(acc[jj], ei + P.eb[j] - 14);
                     if (P.D) {
@@ -500,8 +514,8 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
     P.eb = d.oz_eb;
     P.status = d.status;
     const int KT = kt_elems(bf16 ? 2 : 4);
-    P.Mt = (P.M + kTileRows - 1) / kTileRows;
-    P.Nt = (P.N + kTileRows - 1) / kTileRows;
+    P.Mt = (P.M + kTileM - 1) / kTileM;
+    P.Nt = (P.N + kTileN - 1) / kTileN;
     P.Kt = (P.K + KT - 1) / KT;
     out[s] = P;
 }
@@ -552,15 +566,18 @@ cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cuda
 }
 
 size_t oz_slice_bytes(int rows, int K, bool bf16) {
+    // room for either operand: ceil(rows / 128) tiles of 8 KB cover ceil(rows / 64) of 4 KB
     const int KT = kt_elems(bf16 ? 2 : 4);
-    const size_t Rt = (rows + kTileRows - 1) / kTileRows, Kt = (K + KT - 1) / KT;
-    return (size_t)kS * Rt * Kt * kBlock;
+    const size_t Rt = (rows + kTileM - 1) / kTileM, Kt = (K + KT - 1) / KT;
+    return (size_t)kS * Rt * Kt * kBlockA;
 }
+
+size_t oz_exp_ints(int rows) { return (size_t)((rows + kTileM - 1) / kTileM) * kTileM; }
 
 void oz_tiles(OzProblem& p, bool bf16) {
     const int KT = kt_elems(bf16 ? 2 : 4);
-    p.Mt = (p.M + kTileRows - 1) / kTileRows;
-    p.Nt = (p.N + kTileRows - 1) / kTileRows;
+    p.Mt = (p.M + kTileM - 1) / kTileM;
+    p.Nt = (p.N + kTileN - 1) / kTileN;
     p.Kt = (p.K + KT - 1) / KT;
 }
 
@@ -573,8 +590,8 @@ cudaError_t oz_prepare() {
 cudaError_t launch_oz_gemm(const OzProblem* d_probs, int count, int max_m, int max_n, int max_rows_sliced,
                            bool bf16, unsigned long long timeout_ns, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    const int mt = (max_m + kTileRows - 1) / kTileRows, nt = (max_n + kTileRows - 1) / kTileRows;
-    const int rows = ((max_rows_sliced + kTileRows - 1) / kTileRows) * kTileRows;
+    const int mt = (max_m + kTileM - 1) / kTileM, nt = (max_n + kTileN - 1) / kTileN;
+    const int rows = ((max_rows_sliced + kTileM - 1) / kTileM) * kTileM;
     dim3 sg((rows + 7) / 8, 2, count);
     if (bf16)
         oz_slice_kernel<true><<<sg, 256, 0, st>>>(d_probs);
@@ -622,7 +639,7 @@ extern "C" int mpdo_gemm_tc(int M, int N, int K, const double* A, int lda, const
     oz_tiles(P, bf16);
     const size_t sa = oz_slice_bytes(M, K, bf16), sb = oz_slice_bytes(N, K, bf16);
     unsigned char* buf = nullptr;
-    const size_t ia = (size_t)P.Mt * 128, ib = (size_t)P.Nt * 128;
+    const size_t ia = oz_exp_ints(M), ib = oz_exp_ints(N);
     const size_t bytes = sa + sb + sizeof(int) * (ia + ib) + sizeof(OzProblem) + 256;
     cudaError_t e = cudaMalloc((void**)&buf, bytes);
     if (e != cudaSuccess) {

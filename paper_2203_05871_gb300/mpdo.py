@@ -180,7 +180,7 @@ class Solver:
     def __init__(self, n_qubits: int, batch: int = 1, chi_cap: int = 32, precision: int = FP64,
                  storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 100,
                  jacobi_tol: float = 0.0, barrier_timeout_ms: int = 4000, max_slots: int = 0,
-                 device: Optional[int] = None):
+                 device: Optional[int] = None, trotter_order: int = 2):
         lib = load_library()
         cfg = Config()
         _check(lib.mpdo_config_default(ctypes.byref(cfg)))
@@ -189,6 +189,7 @@ class Solver:
         cfg.force_trace = 1 if force_trace else 0
         cfg.jacobi_max_sweeps, cfg.jacobi_tol = jacobi_max_sweeps, jacobi_tol
         cfg.barrier_timeout_ms, cfg.max_slots = barrier_timeout_ms, max_slots
+        cfg.trotter_order = int(trotter_order)
         if device is None:
             try:
                 import torch

@@ -72,5 +72,5 @@ def test_init_rejects_bad_config_without_gpu(lib):
     assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
     cfg.n_qubits, cfg.chi_cap = 8, 1024
     assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
-    cfg.chi_cap, cfg.trotter_order = 16, 4
+    cfg.chi_cap, cfg.trotter_order = 16, 3
     assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
