@@ -156,3 +156,16 @@ def osee(r, n, bond):
     p = s * s / np.sum(s * s)
     p = p[p > 0.0]
     return float(-np.sum(p * np.log(p)))
+
+
+def graph_rho(n, pairs):
+    """rho = |G><G| of Eq. (graph_state): the state vector of |+x>^n with a
+    controlled-Z (diag(1, 1, 1, -1)) on every listed pair, built directly on
+    the 2^n amplitudes: CZ[j,k] flips the sign where bits j and k are 1."""
+    psi = np.full(2 ** n, 2.0 ** (-n / 2.0), dtype=complex)
+    idx = np.arange(2 ** n)
+    for (j, k) in pairs:
+        bj = (idx >> (n - 1 - j)) & 1
+        bk = (idx >> (n - 1 - k)) & 1
+        psi = np.where((bj & bk) == 1, -psi, psi)
+    return np.outer(psi, psi.conj())

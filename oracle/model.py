@@ -111,6 +111,22 @@ def op_generator(params, b, qa, qb, bond_index, weights):
     return Lbond + weights[qa] * np.kron(La, np.eye(4)) + weights[qb] * np.kron(np.eye(4), Lb)
 
 
+def cz_matrix():
+    """Pauli-basis superoperator of the controlled-Z channel rho -> CZ rho CZ
+    on two sites (Sec. 2.2, Eq. (graph_state)), by explicit traces:
+    G[(a,b), (c,d)] = Tr[(P_a x P_b) CZ (P_c x P_d) CZ] / 4."""
+    cz = np.diag([1.0, 1.0, 1.0, -1.0]).astype(complex)
+    G = np.zeros((16, 16))
+    for a in range(4):
+        for b in range(4):
+            Pab = np.kron(PAULI[a], PAULI[b])
+            for c in range(4):
+                for d in range(4):
+                    Pcd = np.kron(PAULI[c], PAULI[d])
+                    G[a * 4 + b, c * 4 + d] = np.trace(Pab @ cz @ Pcd @ cz).real / 4.0
+    return G
+
+
 def swap_matrix():
     """Pauli-basis SWAP of two sites: |a,b>> -> |b,a>>."""
     S = np.zeros((16, 16))

@@ -178,6 +178,30 @@ def build_gates(wl, b, layers, dt):
     return out
 
 
+def graph_state_ops(n, pairs):
+    """Op list that applies CZ to every listed pair (i, j) of path positions:
+    for j > i + 1 swaps at j-1, ..., i+1 bring qubit j next to i, then CZ on
+    (i, i+1), then the same swaps in reverse order.  Ops as (kind, p)."""
+    ops = []
+    for (i, j) in pairs:
+        i, j = min(i, j), max(i, j)
+        ops += [("swap", p) for p in range(j - 1, i, -1)]
+        ops.append(("cz", i))
+        ops += [("swap", p) for p in range(i + 1, j)]
+    return ops
+
+
+def graph_state(n, pairs, chi_max, cutoff):
+    """The graph state of Sec. 2.2, Eq. (graph_state): every qubit +x, then a
+    controlled-Z on every listed pair, applied as two-site gates (with the
+    truncation rule of App. B) to the Pauli product state."""
+    st = MPOState(*product_state(n, ["+x"] * n))
+    S, CZ = model.swap_matrix(), model.cz_matrix()
+    for kind, p in graph_state_ops(n, pairs):
+        st.apply(p, CZ if kind == "cz" else S, chi_max, cutoff)
+    return st
+
+
 class TEBD:
     """Plain sequential MPO-TEBD for instance ``b`` of a workload."""
 
