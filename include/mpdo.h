@@ -112,6 +112,18 @@ int mpdo_init(mpdo_ctx **out, const mpdo_config *cfg, void *cuda_stream);
  * chi_max > chi_cap, malformed init string), ECUDA. */
 int mpdo_build_gates(mpdo_ctx *ctx, const mpdo_model *model, double dt);
 
+/* Replace every instance's state by the graph state of Sec. 2.2, Eq.
+ * (graph_state): all qubits +x, then a controlled-Z on every pair (i, j) of
+ * pairs[n_pairs][2] (host memory; path positions, i != j; the CZs commute, so
+ * the order is immaterial).  Each CZ runs as a two-site gate (its Pauli-basis
+ * superoperator, a signed permutation) through the same merge / QR / SVD /
+ * truncation path as a Trotter step, with swap gates bringing j next to i; the
+ * state is exact while each instance's chi_max holds the graph state's bond
+ * dimensions (at most 4^k across a cut crossed by k pairs).  Call after
+ * mpdo_build_gates (which sets the Pauli product state instead).  EINVAL,
+ * ESTATE, and the status errors of mpdo_trotter_step. */
+int mpdo_init_graph_state(mpdo_ctx *ctx, const int *pairs, int n_pairs);
+
 /* Advance every instance by n_steps Trotter steps (cfg.trotter_order).  Per op:
  * merge the two sites, apply the gate, weight by the left Schmidt values,
  * Householder QR (only R is kept), SVD of R (FP64 one-sided Jacobi on its

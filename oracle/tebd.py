@@ -205,7 +205,8 @@ def graph_state(n, pairs, chi_max, cutoff):
 class TEBD:
     """Plain sequential MPO-TEBD for instance ``b`` of a workload."""
 
-    def __init__(self, wl, b=0, state: Optional[MPOState] = None, force_trace=True, tol=None, order=2):
+    def __init__(self, wl, b=0, state: Optional[MPOState] = None, force_trace=True, tol=None, order=2,
+                 svd_impl="jacobi"):
         self.wl = wl
         self.b = b
         self.layers = schedule.step_layers_order(wl.n, wl.bonds, order)
@@ -215,6 +216,7 @@ class TEBD:
         self.state = state if state is not None else MPOState(*product_state(wl.n, wl.init))
         self.force_trace = force_trace
         self.tol = tol
+        self.svd_impl = svd_impl   # "lapack": numpy's gesdd route (large bond matrices)
         self.k_log: List[int] = []
         self.max_discarded = 0.0
         self.trace_log: List[float] = []
@@ -225,7 +227,7 @@ class TEBD:
         for layer, gl in zip(self.layers, self.gates):
             for op, G in zip(layer, gl):
                 fk = next(forced_k) if forced_k is not None else None
-                k, dw = self.state.apply(op[1], G, self.chi_max, self.cutoff, fk, self.tol)
+                k, dw = self.state.apply(op[1], G, self.chi_max, self.cutoff, fk, self.tol, self.svd_impl)
                 self.k_log.append(k)
                 self.max_discarded = max(self.max_discarded, dw)
         if self.force_trace:

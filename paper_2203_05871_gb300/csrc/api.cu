@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -769,6 +770,112 @@ int mpdo_build_gates(mpdo_ctx* c, const mpdo_model* m, double dt) {
     c->forced.clear();
     c->forced_steps = 0;
     return MPDO_OK;
+}
+
+int mpdo_init_graph_state(mpdo_ctx* c, const int* pairs, int n_pairs) {
+    if (!c) return fail(MPDO_EINVAL, "ctx is NULL");
+    CU(cudaSetDevice(c->dev));
+    if (!c->built) return fail(MPDO_ESTATE, "mpdo_build_gates must come first");
+    if (n_pairs < 0 || (n_pairs > 0 && !pairs)) return fail(MPDO_EINVAL, "pairs must hold n_pairs >= 0 pairs");
+    const int N = c->N, B = c->B;
+    for (int k = 0; k < n_pairs; ++k) {
+        const int i = pairs[2 * k], j = pairs[2 * k + 1];
+        if (i < 0 || j < 0 || i >= N || j >= N || i == j) return fail(MPDO_EINVAL, "pair indices out of range or i == j");
+    }
+    // |+x> on every qubit: site vector (1, 1, 0, 0) / sqrt2, bond dimensions 1
+    const double r2 = 1.0 / std::sqrt(2.0);
+    std::vector<double> v0((size_t)B * N * 4, 0.0);
+    for (size_t q = 0; q < (size_t)B * N; ++q) v0[4 * q] = v0[4 * q + 1] = r2;
+    CU(cudaMemsetAsync(c->d_sites, 0, site_esize(c) * (size_t)B * N * site_elems(c), c->st));
+    CU(cudaMemcpyAsync(c->d_one_a, v0.data(), sizeof(double) * v0.size(), cudaMemcpyHostToDevice, c->st));
+    init_product_kernel<<<B, 64, 0, c->st>>>(c->d_sites, sites_f32(c), c->d_one_a, N, c->cap);
+    CU(cudaGetLastError());
+    std::vector<double> ones((size_t)B * N * c->cap, 1.0);
+    CU(cudaMemcpyAsync(c->d_lam, ones.data(), sizeof(double) * ones.size(), cudaMemcpyHostToDevice, c->st));
+    c->h_dims.assign((size_t)B * (N + 1), 1);
+    CU(cudaMemcpyAsync(c->d_dims, c->h_dims.data(), sizeof(int) * c->h_dims.size(), cudaMemcpyHostToDevice, c->st));
+    CU(cudaMemsetAsync(c->d_status, 0, sizeof(int) * B, c->st));
+    CU(cudaMemsetAsync(c->d_maxdisc, 0, sizeof(double) * B, c->st));
+    CU(cudaStreamSynchronize(c->st));
+    ++c->gen;
+    if (n_pairs == 0) return MPDO_OK;
+    // Pauli-basis superoperators: CZ (rho -> CZ rho CZ, by traces of Pauli products)
+    // and SWAP, as 16 x 16 two-site gates G[(a,b), (c,d)]
+    using cd = std::complex<double>;
+    const cd I(0.0, 1.0);
+    const cd P[4][2][2] = {{{1, 0}, {0, 1}}, {{0, 1}, {1, 0}}, {{0, -I}, {I, 0}}, {{1, 0}, {0, -1}}};
+    const double czd[4] = {1.0, 1.0, 1.0, -1.0};
+    std::vector<double> cz(256, 0.0), sw(256, 0.0);
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b)
+            for (int cc = 0; cc < 4; ++cc)
+                for (int d = 0; d < 4; ++d) {
+                    // Tr[(P_a x P_b) CZ (P_c x P_d) CZ] / 4; CZ is diagonal
+                    cd tr = 0.0;
+                    for (int x = 0; x < 4; ++x)
+                        for (int y = 0; y < 4; ++y) {
+                            const cd pab = P[a][x >> 1][y >> 1] * P[b][x & 1][y & 1];
+                            const cd pcd = P[cc][y >> 1][x >> 1] * P[d][y & 1][x & 1];
+                            tr += pab * czd[y] * pcd * czd[x];
+                        }
+                    cz[(a * 4 + b) * 16 + cc * 4 + d] = tr.real() / 4.0;
+                }
+    for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) sw[(b * 4 + a) * 16 + a * 4 + b] = 1.0;
+    // op list: per pair, swaps bring j next to i, CZ on (i, i+1), swaps back
+    std::vector<Layer> L;
+    std::vector<int> at(N);
+    for (int q = 0; q < N; ++q) at[q] = q;
+    auto push = [&](int kind, int p) {
+        L.push_back(Layer{Op{kind, p, at[p], at[p + 1], -1, 0.0}});
+        if (kind == 1) std::swap(at[p], at[p + 1]);
+    };
+    for (int k = 0; k < n_pairs; ++k) {
+        const int i = std::min(pairs[2 * k], pairs[2 * k + 1]), j = std::max(pairs[2 * k], pairs[2 * k + 1]);
+        for (int p = j - 1; p >= i + 1; --p) push(1, p);
+        push(0, i);
+        for (int p = i + 1; p <= j - 1; ++p) push(1, p);
+    }
+    const int nops = (int)L.size();
+    std::vector<double> hg((size_t)B * nops * 256);
+    for (int b = 0; b < B; ++b)
+        for (int o = 0; o < nops; ++o)
+            std::copy_n((L[o][0].kind == 0 ? cz : sw).data(), 256, hg.data() + ((size_t)b * nops + o) * 256);
+    double* d_g = nullptr;
+    CU(dalloc(&d_g, hg.size()));
+    CU(cudaMemcpyAsync(d_g, hg.data(), sizeof(double) * hg.size(), cudaMemcpyHostToDevice, c->st));
+    // run the ops through the step's machinery on the graph-state op list
+    std::vector<Layer> keep_layers;
+    keep_layers.swap(c->layers);
+    std::vector<int> keep_op0;
+    keep_op0.swap(c->layer_op0);
+    const int keep_n_ops = c->n_ops;
+    double* keep_gates = c->d_gates;
+    const int keep_forced = c->forced_steps;
+    c->layers = L;
+    c->layer_op0.resize(nops);
+    for (int o = 0; o < nops; ++o) c->layer_op0[o] = o;
+    c->n_ops = nops;
+    c->d_gates = d_g;
+    c->forced_steps = 0;
+    int rc = MPDO_OK;
+    for (int li = 0; li < nops && rc == MPDO_OK; ++li) {
+        const std::vector<Item> items = layer_items(c, li);
+        const size_t cs = (size_t)chunk_ops(c);
+        for (size_t s0 = 0; s0 < items.size() && rc == MPDO_OK; s0 += cs) {
+            std::vector<Item> chunk(items.begin() + s0, items.begin() + std::min(items.size(), s0 + cs));
+            rc = run_chunk(c, chunk, 0, nullptr, nullptr, false);
+        }
+    }
+    cudaStreamSynchronize(c->st);
+    c->layers.swap(keep_layers);
+    c->layer_op0.swap(keep_op0);
+    c->n_ops = keep_n_ops;
+    c->d_gates = keep_gates;
+    c->forced_steps = keep_forced;
+    cudaFree(d_g);
+    if (rc) return rc;
+    return check_status_code(c);
 }
 
 int mpdo_trotter_step(mpdo_ctx* c, int n_steps) {

@@ -91,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         "mpdo_force_ranks": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
         "mpdo_inject_fault": (ctypes.c_int, [vp, ctypes.c_int]),
         "mpdo_renyi2": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "mpdo_init_graph_state": (ctypes.c_int, [vp, _ip, ctypes.c_int]),
         "mpdo_gemm_tc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int,
                                         vp, ctypes.c_int, ctypes.c_int, vp]),
         "mpdo_osee": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
@@ -115,7 +116,7 @@ def exported_symbols() -> list[str]:
             "mpdo_measure_1q",
             "mpdo_measure_2q", "mpdo_status", "mpdo_set_state", "mpdo_get_state", "mpdo_op_counts",
             "mpdo_rank_log", "mpdo_force_ranks", "mpdo_autotune", "mpdo_gates", "mpdo_schedule", "mpdo_profile_enable",
-            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_renyi2", "mpdo_osee", "mpdo_gemm_tc", "mpdo_grad_forward",
+            "mpdo_profile_read", "mpdo_profile_sweeps", "mpdo_profile_sweeps_critical", "mpdo_measure_1q_noalloc", "mpdo_inject_fault", "mpdo_renyi2", "mpdo_osee", "mpdo_gemm_tc", "mpdo_init_graph_state", "mpdo_grad_forward",
             "mpdo_grad_backward", "mpdo_grad", "mpdo_last_error", "mpdo_destroy"]
 
 
@@ -247,6 +248,11 @@ class Solver:
         m.init_pauli = init
         _check(self._lib.mpdo_build_gates(self._h, ctypes.byref(m), float(wl.dt if dt is None else dt)))
         self._n_bonds = len(wl.bonds)
+
+    def init_graph_state(self, pairs):
+        """Graph state of Sec. 2.2: +x everywhere, then CZ on every pair."""
+        p = _as(pairs, np.int32).reshape(-1, 2)
+        _check(self._lib.mpdo_init_graph_state(self._h, _ptr(p, ctypes.c_int) if len(p) else None, len(p)))
 
     def step(self, n_steps: int = 1, check: bool = True, graph: bool = False):
         """n_steps Trotter steps (graph=True: replay the step captured as a CUDA graph)."""
