@@ -53,6 +53,7 @@
 #include <mpdo.h>
 
 #include <cuda_bf16.h>
+#include <float.h>
 
 #include "internal.h"
 
@@ -494,6 +495,14 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
             P.ldd = ld;
             P.d_f32 = 1;
             break;
+        case OZ_GRAM:    // M = W W^T, for ops the FP64 pass has not yet shown converged
+            P.M = P.N = (d.fp64_done && *d.fp64_done) ? 0 : d.c;
+            P.K = d.L;
+            P.A = rowmajor(d.W, 0, ld);
+            P.B = rowmajor(d.W, 0, ld);
+            P.C = d.E;
+            P.ldc = ld;
+            break;
         default:         // OZ_W: W = Q W0
             P.M = d.c;
             P.N = d.L;
@@ -546,7 +555,75 @@ __global__ void __launch_bounds__(256) gate_weight_kernel(const OpDesc* descs, i
     }
 }
 
+// One CTA per op: the FP64 pass's convergence test on the Gram matrix M (in
+// d.E).  Rows with M_ii <= eps^2 sum M are numerical zeros (never rotated);
+// once a sweep has settled, pairs of two rows below the (chi_max +
+// max(16, chi_max / 8))-th largest norm are not needed orthogonal (the FP64
+// pass skips them), unless every vector is kept (full_svd).
+__global__ void __launch_bounds__(1024) gram_check_kernel(const OpDesc* descs, double tol, int ldm) {
+    const OpDesc& d = descs[blockIdx.x];
+    if (!d.fp64_done || *d.fp64_done) return;
+    const int c = d.c;
+    const double* M = d.E;
+    __shared__ double s_tot, s_thr;
+    __shared__ double red[32];
+    __shared__ int cnt[32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int i = threadIdx.x; i < c; i += blockDim.x) t += M[(size_t)i * ldm + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        s_tot = tot;
+        s_thr = 0.0;
+    }
+    __syncthreads();
+    // threshold of the discarded rows: the kk-th largest diagonal entry (bisection
+    // on the bit patterns of the non-negative doubles, every thread the same value)
+    const int kk = d.chi_max + (d.chi_max / 8 > 16 ? d.chi_max / 8 : 16);
+    if (!d.full_svd && kk < c) {
+        unsigned long long x = 0ull;
+        for (int bit = 62; bit >= 0; --bit) {
+            const unsigned long long cand = x | (1ull << bit);
+            int n = 0;
+            for (int i = threadIdx.x; i < c; i += blockDim.x)
+                n += (unsigned long long)__double_as_longlong(fmax(M[(size_t)i * ldm + i], 0.0)) >= cand;
+            n = __reduce_add_sync(0xffffffffu, n);
+            if (lane == 0) cnt[warp] = n;
+            __syncthreads();
+            int tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += cnt[w];
+            __syncthreads();
+            if (tot >= kk) x = cand;
+        }
+        if (threadIdx.x == 0) s_thr = __longlong_as_double((long long)x);
+        __syncthreads();
+    }
+    const double floor2 = DBL_EPSILON * DBL_EPSILON * s_tot, thr = s_thr;
+    bool bad = false;
+    for (int e = threadIdx.x; e < c * c && !bad; e += blockDim.x) {
+        const int i = e / c, j = e % c;
+        if (j <= i) continue;
+        const double a = M[(size_t)i * ldm + i], b = M[(size_t)j * ldm + j];
+        if (a <= floor2 || b <= floor2) continue;
+        if (a < thr && b < thr) continue;
+        const double g = M[(size_t)i * ldm + j];
+        if (!(fabs(g) <= tol * sqrt(a) * sqrt(b))) bad = true;
+    }
+    if (__syncthreads_or(bad) == 0 && threadIdx.x == 0) *d.fp64_done = 1;
+}
+
 }  // namespace
+
+cudaError_t launch_gram_check(const OpDesc* d_desc, int nops, double tol, int ld, cudaStream_t st) {
+    if (nops <= 0) return cudaSuccess;
+    gram_check_kernel<<<nops, 1024, 0, st>>>(d_desc, tol, ld);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* probs, int chi_cap, bool bf16,
                           unsigned long long timeout_ns, cudaStream_t st) {

@@ -1,9 +1,11 @@
 """The adjoint at the gradient workload's geometry: N = 24 ring (closing bond
 through swap gates, 91 ops per step), chi_max = 64, cutoff 1e-10, dt = 0.05,
-mixed contractions with the FP64 SVD, from a seeded random MPO at chi = 64;
-loss = sum_{i<j} connected <Z_i Z_j> at the final time.  Random directional
-derivatives of the gradient against central finite differences (h = 1e-6) of
-the forward run with its ranks held fixed."""
+from a physical entangled start (the ring's graph state, bond dimension 16)
+under a seeded model with every term switched on, so that the two steps
+truncate at chi = 64; loss = sum_{i<j} connected <Z_i Z_j> at the final time.
+Random directional derivatives of the gradient against central finite
+differences (h = 1e-6) of the forward run with its ranks held fixed, FP64 and
+mixed contractions."""
 import numpy as np
 import pytest
 
@@ -34,9 +36,8 @@ def _moved(wl, v, h):
 @pytest.mark.parametrize("precision", ["tf32", "fp64"])
 def test_ring24_directional_derivatives(precision):
     from paper_2203_05871_gb300 import FP64, MIXED_TF32, Solver
-    wl = W.uniform_model("ring24", 24, W.ring_bonds(24), chi_max=64, cutoff=1e-10, dt=0.05, steps=2)
+    wl = W.random_model(24, W.ring_bonds(24), 2203058714, chi_max=64, cutoff=1e-10, dt=0.05, steps=2)
     n, nb, steps = 24, len(wl.bonds), 2
-    dims, tens = W.random_mpo_state(n, 64, seed=2203058714, decay=0.02)
     zb = np.zeros((1, n))
     wb = np.triu(np.ones((1, n, n)), 1)
     pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
@@ -47,7 +48,7 @@ def test_ring24_directional_derivatives(precision):
 
     def start(w):
         s.build_gates(w)
-        s.set_state(0, dims, tens)
+        s.init_graph_state(w.bonds)
 
     start(wl)
     s.grad_forward(steps)
