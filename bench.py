@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chain20_chi256")
     ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--mixed-kind", default="tf32", choices=["tf32", "bf16"],
+                    help="tensor kind of the mixed path's slice products (MPDO_MIXED_TF32 / MPDO_MIXED_BF16X3)")
     ap.add_argument("--per-gate-steps", type=int, default=1,
                     help="timed steps of the FP64 path with one op in flight (0: skip)")
     ap.add_argument("--batched-steps", type=int, default=1,
@@ -289,7 +291,7 @@ def run_arm(args, precision, world, dist, local, workload=None, steps=None, warm
     """Time Trotter steps of one precision on one workload; returns a result dict."""
     import numpy as np
     import torch
-    from paper_2203_05871_gb300 import FP64, MIXED_TF32, Solver
+    from paper_2203_05871_gb300 import FP64, MIXED_BF16X3, MIXED_TF32, Solver
 
     workload = workload or args.workload
     steps = args.steps if steps is None else steps
@@ -297,8 +299,9 @@ def run_arm(args, precision, world, dist, local, workload=None, steps=None, warm
     e2e_steps = args.e2e_steps if e2e_steps is None else e2e_steps
     wl, states, cap = make_workload(workload)
     stream = torch.cuda.Stream()
+    mixed = MIXED_BF16X3 if args.mixed_kind == "bf16" else MIXED_TF32
     s = Solver(wl.n, batch=wl.batch, chi_cap=cap, stream=stream,
-               precision=FP64 if precision == "fp64" else MIXED_TF32, max_slots=max_slots)
+               precision=FP64 if precision == "fp64" else mixed, max_slots=max_slots)
     s.build_gates(wl)
     tuned = None
     if autotune and not args.no_autotune:
@@ -377,19 +380,27 @@ def measured_peaks():
         return {}
 
 
-def contraction_roofline(prof):
-    """tcgen05 merge + gate and reconstruct kernels against the TF32 tensor peak
-    (measured BF16 burst x the nominal TF32 / BF16 ratio 1.1 / 2.25)."""
+SLICE_PRODUCTS = 21   # slice pairs (t, u), t + u <= 5, per useful multiply-add of the tensor-core products
+
+
+def contraction_roofline(prof, kind):
+    """The tensor-core contractions (merge + reconstruct, oz_gemm_kernel with its
+    slicing kernels) against the tensor peak of their kind: executed flops = 21
+    slice products per useful flop (the hardware's work), with the useful rate
+    beside it."""
     fl = prof["merge_gate"]["flops"] + prof["reconstruct"]["flops"]
     ms = prof["merge_gate"]["ms"] + prof["reconstruct"]["ms"]
     bf16 = measured_peaks().get("bf16_tflops")
-    peak = bf16 * 1.1 / 2.25 if bf16 else 1900.0 * 1.1 / 2.25
-    achieved = fl / (ms / 1e3) / 1e12 if ms > 0 else None
-    return {"kernel": "tcgen05 merge+gate and reconstruct (TF32, 3-way operand split)", "bound": "tensor",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak if achieved else None, "traffic": None,
-            "note": "useful flops (each is 3 TF32 products of the split operands); peak = measured bf16 burst "
-                    "x 1.1/2.25 (nominal TF32/BF16)" + ("" if bf16 else "; of fallback")}
+    base = bf16 if bf16 else 1900.0
+    peak = base if kind == "bf16" else base * 1.1 / 2.25
+    useful = fl / (ms / 1e3) / 1e12 if ms > 0 else None
+    achieved = useful * SLICE_PRODUCTS if useful else None
+    return {"kernel": "oz_gemm_kernel (merge + reconstruct, incl. slicing and the gate/weight kernel)",
+            "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "traffic": None, "useful_tflops": useful,
+            "note": "achieved = 21 slice products x useful flops (32 cl cm cr + 512 cl cr merge, 32 cl cr k "
+                    "reconstruct) / CUDA-event time of the merge and reconstruct stages; peak = measured bf16 burst"
+                    + (" x 1.1/2.25 (nominal TF32/BF16)" if kind != "bf16" else "") + ("" if bf16 else ", of fallback")}
 
 
 def qr_roofline(prof):
@@ -522,7 +533,8 @@ def main():
     e2e_value = world * n_ops * args.e2e_steps / (head["e2e_ms"] / 1e3) if args.e2e_steps > 0 else None
     prof = head["prof"]
     launches = sum(v["launches"] * KERNELS_PER_PROFILED_LAUNCH.get(k, 1) for k, v in prof.items())
-    dtype = ("mixed: tcgen05 tf32x3 contractions (fp64 re-accumulated), fp32-preconditioned fp64 QR + Jacobi SVD"
+    dtype = (("mixed: tcgen05 %s slice products (six 8-bit slices, exact level sums, fp64 re-accumulated) for the "
+              "contractions and preconditioner GEMMs, fp32-preconditioned fp64 QR + Jacobi SVD" % args.mixed_kind)
              if hp == "mixed" else "f64")
     line = {
         "metric": "gate_applications_per_sec", "value": hs["value"], "unit": "gate-applications/s",
@@ -548,7 +560,7 @@ def main():
                                     prof["jacobi_svd"]["critical_sweeps_fp32"] / prof["jacobi_svd"]["chunks"]]
                                    if prof["jacobi_svd"].get("chunks") else None),
         "roofline": truncation_roofline(prof, hp),
-        "roofline_contraction": contraction_roofline(prof) if hp == "mixed" else None,
+        "roofline_contraction": contraction_roofline(prof, args.mixed_kind) if hp == "mixed" else None,
         "roofline_qr": qr_roofline(prof),
         "autotune": {"jacobi_rows_per_block": head["tuned"],
                      "note": "(chi_l x chi_r): [FP64 pass, FP32 pass], measured before the timed steps"},

@@ -65,7 +65,7 @@ int release_slots(mpdo_ctx* c) {
     void* ptrs[] = {c->d_thetap, c->d_W,    c->d_Z,     c->d_Yk,    c->d_snorm, c->d_desc,  c->d_cta,
                     c->d_sync,   c->d_sweeps, c->d_pre_ok, c->d_W0,  c->d_E,     c->d_Q,     c->d_W32,
                     c->d_U32,    c->d_gemm,  c->d_copy,  c->d_oz_as, c->d_oz_bs, c->d_oz_ea, c->d_oz_eb,
-                    c->d_oz,     c->d_done};
+                    c->d_oz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     c->d_thetap = c->d_W = c->d_Z = c->d_Yk = c->d_snorm = nullptr;
@@ -76,7 +76,6 @@ int release_slots(mpdo_ctx* c) {
     c->d_oz_as = c->d_oz_bs = nullptr;
     c->d_oz_ea = c->d_oz_eb = nullptr;
     c->d_oz = nullptr;
-    c->d_done = nullptr;
     if (c->h_gemm) cudaFreeHost(c->h_gemm);
     c->h_gemm = nullptr;
     if (c->h_copy) cudaFreeHost(c->h_copy);
@@ -142,7 +141,6 @@ int alloc_slots(mpdo_ctx* c, int want) {
         CU(dalloc(&c->d_oz_ea, (size_t)s * oz_exp_ints(c->ld)));
         CU(dalloc(&c->d_oz_eb, (size_t)s * oz_exp_ints(c->ld)));
         CU(dalloc(&c->d_oz, (size_t)s));
-        CU(dalloc(&c->d_done, (size_t)s));
     }
     return MPDO_OK;
 }
@@ -277,7 +275,6 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d) {
     d.E = c->mixed ? c->d_E + (size_t)s * mat : nullptr;
     d.Q = c->mixed ? c->d_Q + (size_t)s * mat : nullptr;
     d.Zinit = nullptr;
-    d.fp64_done = c->mixed ? c->d_done + s : nullptr;
     d.oz_as = c->mixed ? c->d_oz_as + (size_t)s * c->oz_slot_bytes : nullptr;
     d.oz_bs = c->mixed ? c->d_oz_bs + (size_t)s * c->oz_slot_bytes : nullptr;
     d.oz_ea = c->mixed ? c->d_oz_ea + (size_t)s * oz_exp_ints(ld) : nullptr;
@@ -357,7 +354,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
     auto plan = [&](bool fp32, int* hbase, int& total) -> int {
         return plan_jacobi(c, c->h_desc, nops, fp32, hbase, total);
     };
-    auto run_jacobi = [&](bool fp32, int slot, int sweeps = 0, bool partial = false) -> int {
+    auto run_jacobi = [&](bool fp32, int slot) -> int {
         int total = 0;
         int* hbase = c->h_cta + (size_t)slot * (2 * gcap + c->slots);
         int* dbase = c->d_cta + (size_t)slot * (2 * gcap + c->slots);
@@ -365,9 +362,9 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         if (rc) return rc;
         CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
         CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
-        if (sweeps <= 0) sweeps = fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps;
-        CU(launch_jacobi(c->d_desc, nops, dbase, dbase + total, dbase + 2 * total, c->d_sync, total, sweeps,
-                         fp32 ? 0.0 : fp64_jacobi_tol(c), timeout_ns, ld, fp32, c->st, partial));
+        CU(launch_jacobi(c->d_desc, nops, dbase, dbase + total, dbase + 2 * total, c->d_sync, total,
+                         fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : fp64_jacobi_tol(c),
+                         timeout_ns, ld, fp32, c->st));
         return MPDO_OK;
     };
     CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, c->st));
@@ -445,18 +442,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         p_gemm.stop();
     }
     ProfScope p_jac(c, K_JACOBI);
-    if (fp64_gram_check(c)) {
-        // one FP64 sweep, the Gram check on the tensor cores, then the remaining
-        // sweeps only for the ops that are not yet orthogonal to the tolerance
-        CU(cudaMemsetAsync(c->d_done, 0, sizeof(int) * nops, c->st));
-        int rc = run_jacobi(false, 0, 1, true);
-        if (rc) return rc;
-        CU(launch_oz_ops(c->d_desc, nops, OZ_GRAM, c->d_oz, cap, c->oz_bf16, timeout_ns, c->st));
-        CU(launch_gram_check(c->d_desc, nops, fp64_jacobi_tol(c), ld, c->st));
-        rc = run_jacobi(false, 0, c->cfg.jacobi_max_sweeps - 1, false);
-        if (rc) return rc;
-    } else {
-        if (c->mixed) CU(cudaMemsetAsync(c->d_done, 0, sizeof(int) * nops, c->st));
+    {
         int rc = run_jacobi(false, 0);
         if (rc) return rc;
     }

@@ -91,7 +91,6 @@ struct mpdo_ctx {
     unsigned char *d_oz_as = nullptr, *d_oz_bs = nullptr;   // [slots] slice blocks of the tensor-core products
     int *d_oz_ea = nullptr, *d_oz_eb = nullptr;             // [slots][4 chi_cap] their exponents
     mpdo::OzProblem* d_oz = nullptr;                        // [slots] problems of one launch
-    int* d_done = nullptr;                                  // [slots] FP64 pass known converged
     size_t oz_slot_bytes = 0;
     double *d_W0 = nullptr, *d_E = nullptr, *d_Q = nullptr;
     float *d_W32 = nullptr, *d_U32 = nullptr;
@@ -204,13 +203,6 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d);
 constexpr double kMixedFinishTol = 1e-10;
 inline double fp64_jacobi_tol(const mpdo_ctx* c) {
     return (c->cfg.jacobi_tol <= 0.0 && c->mixed && !c->full_svd) ? kMixedFinishTol : c->cfg.jacobi_tol;
-}
-// The mixed path's FP64 pass runs one sweep, then checks convergence on the
-// Gram matrix W W^T from the tensor cores (accurate to ~1e-12 relative, far
-// inside the finish tolerance) and runs the remaining sweeps only for the ops
-// that fail it; this replaces the confirming sweep of dot products.
-inline bool fp64_gram_check(const mpdo_ctx* c) {
-    return c->mixed && fp64_jacobi_tol(c) >= 1e-11 && c->cfg.jacobi_max_sweeps > 1;
 }
 
 int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* forced, const TapeSlot* tape,

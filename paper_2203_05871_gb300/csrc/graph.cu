@@ -190,22 +190,9 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_Q, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_W, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
             }
-            if (fp64_gram_check(c)) {
-                CU(cudaMemsetAsync(c->d_done, 0, sizeof(int) * nops, st));
-                CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
-                CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync,
-                                 g->Rj, 1, fp64_jacobi_tol(c), timeout_ns, ld, false, st, true));
-                CU(launch_oz_ops(ch.d_desc, nops, OZ_GRAM, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
-                CU(launch_gram_check(ch.d_desc, nops, fp64_jacobi_tol(c), ld, st));
-                CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
-                CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync,
-                                 g->Rj, c->cfg.jacobi_max_sweeps - 1, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
-            } else {
-                if (c->mixed) CU(cudaMemsetAsync(c->d_done, 0, sizeof(int) * nops, st));
-                CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
-                CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync,
-                                 g->Rj, c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
-            }
+            CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
+            CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync, g->Rj,
+                             c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
             CU(launch_truncate(ch.d_desc, nops, cap, st));
             if (c->mixed)
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_RECON, c->d_oz, cap, c->oz_bf16, timeout_ns, st));

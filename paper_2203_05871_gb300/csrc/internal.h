@@ -78,8 +78,6 @@ struct OpDesc {
     int full_svd;      // 1: orthogonalise every pair of rows (the adjoint needs all singular vectors)
     double* tape_V;    // adjoint recompute: all c sorted right singular vectors (c x n), or nullptr
     double* tape_s;    // adjoint recompute: all c sorted singular values
-    int* fp64_done;        // mixed path: 1 once the FP64 pass is known converged (first sweep, then
-                           // the Gram check); a later FP64 launch skips the op (or nullptr)
     void *oz_as, *oz_bs;   // mixed path: slice blocks of the tensor-core products (oz_gemm.cu)
     int *oz_ea, *oz_eb;    // and their row / column exponents
 };
@@ -153,11 +151,9 @@ cudaError_t jacobi_max_resident(int* blocks);
 // layout documented in jacobi.cu).
 // fp32 = true: the FP32 preconditioning pass on (W32 | U32) (U32 starts as I,
 // W32 is filled from W0, scaled); false: the FP64 pass on (W | Z).
-// partial (FP64 pass only): a sweep limit that is reached is not an error; the
-// op's fp64_done flag records whether it converged instead.
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st, bool partial = false);
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st);
 size_t jacobi_sync_words_per_op();
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
@@ -203,15 +199,9 @@ cudaError_t launch_oz_gemm(const OzProblem* d_probs, int count, int max_m, int m
 // share them): kind OZ_MERGE Theta = A B (then launch_gate_weight applies the
 // gate and the left weights), OZ_RECON B_p' = Theta' Yk^T, OZ_E E = U U^T - I,
 // OZ_Q Q = U - E U / 2, OZ_W W = Q W0.  probs: scratch for nops problems.
-enum { OZ_MERGE = 0, OZ_RECON = 1, OZ_E = 2, OZ_Q = 3, OZ_W = 4, OZ_GRAM = 5 };
+enum { OZ_MERGE = 0, OZ_RECON = 1, OZ_E = 2, OZ_Q = 3, OZ_W = 4 };
 cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* probs, int chi_cap, bool bf16,
                           unsigned long long timeout_ns, cudaStream_t st);
-// Gram check of the mixed path's FP64 pass: with M = W W^T in the op's E
-// buffer (OZ_GRAM, only for ops whose fp64_done is 0), sets fp64_done when
-// every pair of rows that the truncation may keep is orthogonal to tol
-// relative to its norms (|M_ij| <= tol sqrt(M_ii M_jj)), the FP64 pass's own
-// convergence test.
-cudaError_t launch_gram_check(const OpDesc* d_desc, int nops, double tol, int ld, cudaStream_t st);
 // Theta' = G Theta in place in thetap and theta~ = lambda_l Theta' (column-major, Acm)
 cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
 

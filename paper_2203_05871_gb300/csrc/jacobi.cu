@@ -664,8 +664,7 @@ __device__ double kth_largest(const double* v, int c, int kk) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
-                                                       double tol_in, unsigned long long timeout_ns, int ld,
-                                                       int partial) {
+                                                       double tol_in, unsigned long long timeout_ns, int ld) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kF32 = sizeof(T) == 4;
     const int op = cta_op[blockIdx.x];
@@ -673,9 +672,6 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
     const int g = cta_rank[blockIdx.x];
     const int G = group[op];
     const OpDesc& d = descs[op];
-    // an op already known converged (mixed path: earlier FP64 launch, Gram check)
-    // is skipped by every one of its CTAs before any barrier
-    if (!kF32 && d.fp64_done && *(volatile const int*)d.fp64_done) return;
     unsigned* sw = sync + (size_t)op * kSyncWords;
     const int c = d.c, L = d.L;
     int b = kF32 ? d.jb32 : d.jb;
@@ -928,11 +924,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
         if (g == 0 && threadIdx.x == 0) {
             if (!kF32) {
                 if (d.sweeps_out) *d.sweeps_out += used;
-                if (partial) {
-                    if (d.fp64_done) *d.fp64_done = conv ? 1 : 0;
-                } else if (!conv) {
-                    atomicOr(d.status, (int)MPDO_ST_NOCONV);
-                }
+                if (!conv) atomicOr(d.status, (int)MPDO_ST_NOCONV);
             } else {
                 if (d.sweeps_out) *d.sweeps_out += used << 16;   // FP32 sweeps in the high half
                 if (d.pre_ok)
@@ -972,12 +964,11 @@ cudaError_t jacobi_max_resident(int* blocks) {
 
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st, bool partial) {
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st) {
     (void)nops;
     if (grid <= 0) return cudaSuccess;
-    int part = partial ? 1 : 0;
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
-                    (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld, (void*)&part};
+                    (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
     const void* fn = fp32 ? (const void*)jacobi_kernel<float> : (const void*)jacobi_kernel<double>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(fp32 ? kThreads<float> : kThreads<double>), args,
                                        fp32 ? kSmemF32 : kSmemBytes, st);

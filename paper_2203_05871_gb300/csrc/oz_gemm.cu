@@ -53,7 +53,6 @@
 #include <mpdo.h>
 
 #include <cuda_bf16.h>
-#include <float.h>
 
 #include "internal.h"
 
@@ -206,7 +205,49 @@ __device__ __forceinline__ void slice_group(const double* x, int e, uint4* out /
     }
 }
 
-// grid (row groups of 8, 2 = A | B, problems); one warp per row of the operand
+// Exponent and slices of one operand row r held by one thread (strided views:
+// consecutive threads own consecutive rows, so every load is coalesced).
+template <bool kBf16>
+__device__ __forceinline__ void slice_row_thread(const OzOperand& X, int r, bool live, int K, int Kt,
+                                                 unsigned char* out, int* ex, int tile, int Rt) {
+    constexpr int esize = kBf16 ? 2 : 4;
+    constexpr int G = 16 / esize;
+    constexpr int KT = kt_elems(esize);
+    double mx = 0.0;
+    bool bad = false;
+    if (live)
+        for (int k = 0; k < K; ++k) {
+            const double v = oz_load(X, r, k);
+            mx = fmax(mx, fabs(v));
+            bad |= !isfinite(v);
+        }
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    ex[r] = e;
+    const int rt = r / tile, rr = r % tile;
+    const size_t block = (size_t)tile * 64;
+    const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
+    for (int g0 = 0; g0 < Kt * KT; g0 += G) {
+        double x[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int k = g0 + g;
+            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
+        }
+        uint4 sl[kS];
+        slice_group<G, kBf16>(x, e, sl);
+        const int kt = g0 / KT, kk = g0 % KT;
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * block;
+            *reinterpret_cast<uint4*>(blk + within + (size_t)(kk / G) * LBO) = sl[t];
+        }
+    }
+}
+
+// grid (row groups, 2 = A | B, problems).  Views whose rows are contiguous
+// (ks == 1) take one warp per row (lanes along k); the others (a transposed
+// operand, the right site of a merge) one thread per row, 256 rows per block.
 template <bool kBf16>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     constexpr int esize = kBf16 ? 2 : 4;
@@ -221,19 +262,27 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     const int Rt = isB ? P.Nt : P.Mt;
     const int K = P.K, Kt = P.Kt;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int r = blockIdx.x * 8 + warp;
-    if (r >= Rt * tile) return;
     unsigned char* out = static_cast<unsigned char*>(isB ? P.bs : P.as);
     int* ex = isB ? P.eb : P.ea;
+    if (!(X.mode == 0 && X.ks == 1)) {
+        const int r = blockIdx.x * 256 + threadIdx.x;
+        if (r >= Rt * tile) return;
+        slice_row_thread<kBf16>(X, r, r < R, K, Kt, out, ex, tile, Rt);
+        return;
+    }
+    const int r = blockIdx.x * 8 + warp;
+    if (r >= Rt * tile) return;
     const bool live = r < R;
     double mx = 0.0;
+    bool bad = false;
     if (live)
-        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(oz_load(X, r, k)));
+        for (int k = lane; k < K; k += 32) {
+            const double v = oz_load(X, r, k);
+            mx = fmax(mx, fabs(v));          // fmax drops NaN: non-finite rows are flagged apart
+            bad |= !isfinite(v);
+        }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    bool bad = false;
-    if (live)   // a non-finite entry makes the row's slices non-finite (fmax drops NaN)
-        for (int k = lane; k < K; k += 32) bad |= !isfinite(oz_load(X, r, k));
     bad = __any_sync(0xffffffffu, bad);
     int e = 0;
     if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
@@ -246,8 +295,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = g0 + g;
-            x[g] = (live && k < K) ? oz_load(X, r, k) : 0.0;
-            if (bad && live && k < K) x[g] = __longlong_as_double(0x7ff8000000000000ll);
+            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
         }
         uint4 sl[kS];
         slice_group<G, kBf16>(x, e, sl);
@@ -495,14 +543,6 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
             P.ldd = ld;
             P.d_f32 = 1;
             break;
-        case OZ_GRAM:    // M = W W^T, for ops the FP64 pass has not yet shown converged
-            P.M = P.N = (d.fp64_done && *d.fp64_done) ? 0 : d.c;
-            P.K = d.L;
-            P.A = rowmajor(d.W, 0, ld);
-            P.B = rowmajor(d.W, 0, ld);
-            P.C = d.E;
-            P.ldc = ld;
-            break;
         default:         // OZ_W: W = Q W0
             P.M = d.c;
             P.N = d.L;
@@ -555,75 +595,7 @@ __global__ void __launch_bounds__(256) gate_weight_kernel(const OpDesc* descs, i
     }
 }
 
-// One CTA per op: the FP64 pass's convergence test on the Gram matrix M (in
-// d.E).  Rows with M_ii <= eps^2 sum M are numerical zeros (never rotated);
-// once a sweep has settled, pairs of two rows below the (chi_max +
-// max(16, chi_max / 8))-th largest norm are not needed orthogonal (the FP64
-// pass skips them), unless every vector is kept (full_svd).
-__global__ void __launch_bounds__(1024) gram_check_kernel(const OpDesc* descs, double tol, int ldm) {
-    const OpDesc& d = descs[blockIdx.x];
-    if (!d.fp64_done || *d.fp64_done) return;
-    const int c = d.c;
-    const double* M = d.E;
-    __shared__ double s_tot, s_thr;
-    __shared__ double red[32];
-    __shared__ int cnt[32];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    double t = 0.0;
-    for (int i = threadIdx.x; i < c; i += blockDim.x) t += M[(size_t)i * ldm + i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[warp] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double tot = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-        s_tot = tot;
-        s_thr = 0.0;
-    }
-    __syncthreads();
-    // threshold of the discarded rows: the kk-th largest diagonal entry (bisection
-    // on the bit patterns of the non-negative doubles, every thread the same value)
-    const int kk = d.chi_max + (d.chi_max / 8 > 16 ? d.chi_max / 8 : 16);
-    if (!d.full_svd && kk < c) {
-        unsigned long long x = 0ull;
-        for (int bit = 62; bit >= 0; --bit) {
-            const unsigned long long cand = x | (1ull << bit);
-            int n = 0;
-            for (int i = threadIdx.x; i < c; i += blockDim.x)
-                n += (unsigned long long)__double_as_longlong(fmax(M[(size_t)i * ldm + i], 0.0)) >= cand;
-            n = __reduce_add_sync(0xffffffffu, n);
-            if (lane == 0) cnt[warp] = n;
-            __syncthreads();
-            int tot = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += cnt[w];
-            __syncthreads();
-            if (tot >= kk) x = cand;
-        }
-        if (threadIdx.x == 0) s_thr = __longlong_as_double((long long)x);
-        __syncthreads();
-    }
-    const double floor2 = DBL_EPSILON * DBL_EPSILON * s_tot, thr = s_thr;
-    bool bad = false;
-    for (int e = threadIdx.x; e < c * c && !bad; e += blockDim.x) {
-        const int i = e / c, j = e % c;
-        if (j <= i) continue;
-        const double a = M[(size_t)i * ldm + i], b = M[(size_t)j * ldm + j];
-        if (a <= floor2 || b <= floor2) continue;
-        if (a < thr && b < thr) continue;
-        const double g = M[(size_t)i * ldm + j];
-        if (!(fabs(g) <= tol * sqrt(a) * sqrt(b))) bad = true;
-    }
-    if (__syncthreads_or(bad) == 0 && threadIdx.x == 0) *d.fp64_done = 1;
-}
-
 }  // namespace
-
-cudaError_t launch_gram_check(const OpDesc* d_desc, int nops, double tol, int ld, cudaStream_t st) {
-    if (nops <= 0) return cudaSuccess;
-    gram_check_kernel<<<nops, 1024, 0, st>>>(d_desc, tol, ld);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* probs, int chi_cap, bool bf16,
                           unsigned long long timeout_ns, cudaStream_t st) {
