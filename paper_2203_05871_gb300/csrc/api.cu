@@ -416,11 +416,21 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
             fl_qr += 4.0 * d.m * d.n * d.c - 2.0 * (d.m + d.n) * d.c * d.c + 4.0 / 3.0 * d.c * d.c * d.c;
         }
         qr_flops_chunk = fl_qr;
-        CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
-        CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
-        ProfScope p_qr(c, K_QR);
-        CU(launch_qr(c->d_desc, dbase, dbase + total, dbase + 2 * total, c->d_sync, total, timeout_ns, ld, c->st));
-        p_qr.stop();
+        if (c->mixed && qrb_fits(cap)) {
+            // mixed path: blocked QR, trailing updates on the tensor cores
+            int r_max = 1;
+            for (int s = 0; s < nops; ++s) r_max = std::max(r_max, c->h_desc[s].c);
+            ProfScope p_qr(c, K_QR);
+            CU(launch_qr_blocked(c->d_desc, nops, cap, c->d_oz, c->oz_bf16, timeout_ns, c->st, r_max));
+            p_qr.stop();
+        } else {
+            CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
+            CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+            ProfScope p_qr(c, K_QR);
+            CU(launch_qr(c->d_desc, dbase, dbase + total, dbase + 2 * total, c->d_sync, total, timeout_ns, ld,
+                         c->st));
+            p_qr.stop();
+        }
     }
     double fl_gemm = 0.0;
     if (c->mixed) {
@@ -637,7 +647,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
              std::string("device allocation: ") + cudaGetErrorString(e));
         return bail(e == cudaErrorMemoryAllocation ? MPDO_ENOMEM : MPDO_ECUDA);
     }
-    if ((e = oz_prepare()) != cudaSuccess) {
+    if ((e = oz_prepare()) != cudaSuccess || (e = qrb_prepare()) != cudaSuccess) {
         fail(MPDO_ECUDA, std::string("tensor-core kernel set-up: ") + cudaGetErrorString(e));
         return bail(MPDO_ECUDA);
     }

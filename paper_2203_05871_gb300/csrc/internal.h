@@ -162,21 +162,25 @@ cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStr
 // FP64-accurate GEMM on the tensor cores from exact slice products (oz_gemm.cu)
 // ---------------------------------------------------------------------------
 // One operand as a view over (row, k): A's rows are the rows i of A, B's rows
-// the columns j of B.  mode 0: element (r, k) at base[r * rs + k * ks];
-// mode 1 (right site of a merge): element (n, k) at base[(k * 4 + n / cr) * cap + n % cr].
+// the columns j of B.  mode 0: element (r, k) at base[g(r) * rs + k * ks], g(r) =
+// gather[r] (or r when gather is null); mode 1 (right site of a merge): element
+// (n, k) at base[(k * 4 + n / cr) * cap + n % cr].
 struct OzOperand {
     const void* base;
     int f32;             // elements are float (else double)
     long long rs, ks;
     int mode, cr, cap;
+    const int* gather;   // row gather (mode 0), or nullptr
 };
-// C = alpha A B + beta D (- I), C and D row-major (f64 or f32)
+// C = alpha A B + beta D (- I), C and D row-major (f64 or f32); row i of C and D
+// is row c_gather[i] of their storage when c_gather is set
 struct OzProblem {
     int M, N, K;
     const int* Ndyn;     // non-null: N is read on the device (<= N, which sizes the tiles)
     OzOperand A, B;
     void* C;
     int ldc, c_f32;
+    const int* c_gather;
     double alpha, beta;
     const void* D;
     int ldd, d_f32, sub_identity;
@@ -185,6 +189,13 @@ struct OzProblem {
     int Mt, Nt, Kt;      // tiles (128 rows, 64 columns, 64 bytes of K)
     int* status;         // MPDO_ST_TIMEOUT when a wait gives up (or nullptr)
 };
+// tiles of a problem: 128 rows of A, 64 columns of B, 64 bytes of K (32 bf16 or 16 tf32 values)
+__host__ __device__ inline void oz_set_tiles(OzProblem& p, bool bf16) {
+    const int KT = bf16 ? 32 : 16;
+    p.Mt = (p.M + 127) / 128;
+    p.Nt = (p.N + 63) / 64;
+    p.Kt = (p.K + KT - 1) / KT;
+}
 size_t oz_slice_bytes(int rows, int K, bool bf16);   // slice blocks of an operand of rows x K
 size_t oz_exp_ints(int rows);                          // its exponent array (rows rounded up to a tile)
 void oz_tiles(OzProblem& p, bool bf16);
@@ -204,6 +215,20 @@ cudaError_t launch_oz_ops(const OpDesc* d_desc, int nops, int kind, OzProblem* p
                           unsigned long long timeout_ns, cudaStream_t st);
 // Theta' = G Theta in place in thetap and theta~ = lambda_l Theta' (column-major, Acm)
 cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
+
+// Blocked Householder QR of the mixed path (qr_blocked.cu): panels of nb columns
+// chosen by largest norm and factored with pivoting inside the panel in one CTA,
+// compact-WY trailing updates as tensor-core products with FP64-class accuracy.
+// Same output as launch_qr: the rows of R P^T in d.W0.  Scratch: d.W (panel
+// reflectors and products), d.snorm (column norms, permutation), the op's slice
+// buffers.  One panel loop over the chunk (ops with fewer columns idle through it).
+int qrb_panel_width(int chi_cap);
+// the blocked QR needs d.W to hold its scratch (48 ld + 256 doubles of ld^2)
+inline bool qrb_fits(int chi_cap) { return 4 * chi_cap >= 128; }
+cudaError_t qrb_prepare();
+// r_max: the largest min(m, n) of the chunk's ops (<= 0: the capacity 4 chi_cap)
+cudaError_t launch_qr_blocked(const OpDesc* d_desc, int nops, int chi_cap, OzProblem* probs, bool bf16,
+                              unsigned long long timeout_ns, cudaStream_t st, int r_max);
 
 int qr_threads();
 cudaError_t qr_max_resident(int* blocks);

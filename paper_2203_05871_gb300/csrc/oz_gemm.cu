@@ -73,6 +73,7 @@ constexpr int kRangeK = 256;           // K values between accumulator drains
 constexpr int kThreads = 320;
 constexpr int kSmem = kStages * kStageBytes + 1024;
 static_assert(kLevels * kTileN <= 512, "accumulators exceed tensor memory");
+static_assert(kTileM == 128 && kTileN == 64, "oz_set_tiles (internal.h) assumes 128 x 64 tiles");
 constexpr int LBO = 128, SBO = 512;
 
 __host__ __device__ constexpr int kt_elems(int esize) { return 64 / esize; }
@@ -170,7 +171,7 @@ __device__ __forceinline__ double oz_load(const OzOperand& X, int r, int k) {
     if (X.mode == 1)
         i = ((size_t)k * 4 + (size_t)(r / X.cr)) * X.cap + (r % X.cr);
     else
-        i = (size_t)r * X.rs + (size_t)k * X.ks;
+        i = (size_t)(X.gather ? X.gather[r] : r) * X.rs + (size_t)k * X.ks;
     return X.f32 ? (double)static_cast<const float*>(X.base)[i] : static_cast<const double*>(X.base)[i];
 }
 
@@ -205,49 +206,9 @@ __device__ __forceinline__ void slice_group(const double* x, int e, uint4* out /
     }
 }
 
-// Exponent and slices of one operand row r held by one thread (strided views:
-// consecutive threads own consecutive rows, so every load is coalesced).
-template <bool kBf16>
-__device__ __forceinline__ void slice_row_thread(const OzOperand& X, int r, bool live, int K, int Kt,
-                                                 unsigned char* out, int* ex, int tile, int Rt) {
-    constexpr int esize = kBf16 ? 2 : 4;
-    constexpr int G = 16 / esize;
-    constexpr int KT = kt_elems(esize);
-    double mx = 0.0;
-    bool bad = false;
-    if (live)
-        for (int k = 0; k < K; ++k) {
-            const double v = oz_load(X, r, k);
-            mx = fmax(mx, fabs(v));
-            bad |= !isfinite(v);
-        }
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
-    ex[r] = e;
-    const int rt = r / tile, rr = r % tile;
-    const size_t block = (size_t)tile * 64;
-    const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
-    for (int g0 = 0; g0 < Kt * KT; g0 += G) {
-        double x[G];
-#pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const int k = g0 + g;
-            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
-        }
-        uint4 sl[kS];
-        slice_group<G, kBf16>(x, e, sl);
-        const int kt = g0 / KT, kk = g0 % KT;
-#pragma unroll
-        for (int t = 0; t < kS; ++t) {
-            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * block;
-            *reinterpret_cast<uint4*>(blk + within + (size_t)(kk / G) * LBO) = sl[t];
-        }
-    }
-}
-
-// grid (row groups, 2 = A | B, problems).  Views whose rows are contiguous
-// (ks == 1) take one warp per row (lanes along k); the others (a transposed
-// operand, the right site of a merge) one thread per row, 256 rows per block.
+// grid (row groups of 8, 2 = A | B, problems); one warp per row of the operand
+// (lanes along k).  (One thread per row, which makes the loads of a transposed
+// operand coalesced, measured 2.6x slower: too few threads per operand.)
 template <bool kBf16>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     constexpr int esize = kBf16 ? 2 : 4;
@@ -264,12 +225,6 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* out = static_cast<unsigned char*>(isB ? P.bs : P.as);
     int* ex = isB ? P.eb : P.ea;
-    if (!(X.mode == 0 && X.ks == 1)) {
-        const int r = blockIdx.x * 256 + threadIdx.x;
-        if (r >= Rt * tile) return;
-        slice_row_thread<kBf16>(X, r, r < R, K, Kt, out, ex, tile, Rt);
-        return;
-    }
     const int r = blockIdx.x * 8 + warp;
     if (r >= Rt * tile) return;
     const bool live = r < R;
@@ -467,13 +422,14 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
                     const int j = nt * kTileN + half * 32 + jj;
                     if (j >= N) continue;
                     double v = P.alpha * ldexp(acc[jj], ei + P.eb[j] - 14);
+                    const size_t row = P.c_gather ? (size_t)P.c_gather[i] : (size_t)i;
                     if (P.D) {
-                        const size_t di = (size_t)i * P.ldd + j;
+                        const size_t di = row * P.ldd + j;
                         v += P.beta * (P.d_f32 ? (double)static_cast<const float*>(P.D)[di]
                                                : static_cast<const double*>(P.D)[di]);
                     }
                     if (P.sub_identity && i == j) v -= 1.0;
-                    const size_t ci = (size_t)i * P.ldc + j;
+                    const size_t ci = row * P.ldc + j;
                     if (P.c_f32)
                         static_cast<float*>(P.C)[ci] = (float)v;
                     else
@@ -497,10 +453,10 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
     const int ld = 4 * cap;
     OzProblem P{};
     auto rowmajor = [](const void* base, int f32, long long ld_) {   // (r, k) at r * ld + k
-        return OzOperand{base, f32, ld_, 1, 0, 1, 1};
+        return OzOperand{base, f32, ld_, 1, 0, 1, 1, nullptr};
     };
     auto colmajor = [](const void* base, int f32, long long ld_) {   // (r, k) at k * ld + r
-        return OzOperand{base, f32, 1, ld_, 0, 1, 1};
+        return OzOperand{base, f32, 1, ld_, 0, 1, 1, nullptr};
     };
     switch (kind) {
         case OZ_MERGE:   // Theta[(l, s1), (s2, r)] = sum_m A[(l, s1), m] B[m, (s2, r)]
@@ -508,7 +464,7 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
             P.K = d.cm;
             P.N = 4 * d.cr;
             P.A = rowmajor(d.A, d.site_f32, cap);
-            P.B = OzOperand{d.B, d.site_f32, 0, 0, 1, d.cr, cap};
+            P.B = OzOperand{d.B, d.site_f32, 0, 0, 1, d.cr, cap, nullptr};
             P.C = d.thetap;
             P.ldc = ld;
             break;
@@ -562,10 +518,7 @@ __global__ void oz_prep_kernel(const OpDesc* descs, int nops, int kind, OzProble
     P.ea = d.oz_ea;
     P.eb = d.oz_eb;
     P.status = d.status;
-    const int KT = kt_elems(bf16 ? 2 : 4);
-    P.Mt = (P.M + kTileM - 1) / kTileM;
-    P.Nt = (P.N + kTileN - 1) / kTileN;
-    P.Kt = (P.K + KT - 1) / KT;
+    oz_set_tiles(P, bf16 != 0);
     out[s] = P;
 }
 
@@ -623,12 +576,7 @@ size_t oz_slice_bytes(int rows, int K, bool bf16) {
 
 size_t oz_exp_ints(int rows) { return (size_t)((rows + kTileM - 1) / kTileM) * kTileM; }
 
-void oz_tiles(OzProblem& p, bool bf16) {
-    const int KT = kt_elems(bf16 ? 2 : 4);
-    p.Mt = (p.M + kTileM - 1) / kTileM;
-    p.Nt = (p.N + kTileN - 1) / kTileN;
-    p.Kt = (p.K + KT - 1) / KT;
-}
+void oz_tiles(OzProblem& p, bool bf16) { oz_set_tiles(p, bf16); }
 
 cudaError_t oz_prepare() {
     cudaError_t e = cudaFuncSetAttribute(oz_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
@@ -680,8 +628,8 @@ extern "C" int mpdo_gemm_tc(int M, int N, int K, const double* A, int lda, const
     P.M = M;
     P.N = N;
     P.K = K;
-    P.A = OzOperand{A, 0, lda, 1, 0, 1, 1};
-    P.B = OzOperand{B, 0, 1, ldb, 0, 1, 1};
+    P.A = OzOperand{A, 0, lda, 1, 0, 1, 1, nullptr};
+    P.B = OzOperand{B, 0, 1, ldb, 0, 1, 1, nullptr};
     P.C = C;
     P.ldc = ldc;
     P.alpha = 1.0;

@@ -5,8 +5,12 @@ state at chi = 64 (the product state evolved four steps of 0.3 by the same
 model; its Schmidt spectra have no degeneracy at the cut, so the truncation
 with the ranks held fixed is a smooth map); loss = sum_{i<j} connected
 <Z_i Z_j> after two steps.  Random directional derivatives of the gradient
-against central finite differences (h = 1e-6) of the forward run with its
-ranks held fixed, FP64 and mixed contractions."""
+against central finite differences of the forward run with its ranks held
+fixed, FP64 and mixed contractions.  The step is h = 1e-4: the directional
+derivatives are ~5e-4 while the loss carries ~1e-12 of rounding from the SVDs,
+so at h = 1e-6 the difference quotient itself is noisy at 1e-6 (measured: two
+precisions' quotients differ by 6e-7); at 1e-4 rounding contributes ~1e-8
+and the truncation error (h^2 times the third derivative) stays below that."""
 import numpy as np
 import pytest
 
@@ -70,7 +74,7 @@ def test_ring24_directional_derivatives(precision):
 
     assert abs(loss(wl) - L[0]) <= 1e-9 * max(1.0, abs(L[0]))
     rng = np.random.default_rng(24)
-    h = 1e-6
+    h = 1e-4
     for trial in range(2):
         v = np.zeros(6 * n + 2 * nb)
         for k in (0, 2, 3, 5):                      # h_x, h_z, g0, g2 per qubit
@@ -81,4 +85,4 @@ def test_ring24_directional_derivatives(precision):
         ad = float(g[0] @ v)
         print(f"ring24 chi64 {precision}: direction {trial}: adjoint {ad:.10e}, finite difference {fd:.10e}, "
               f"|d| = {abs(ad - fd):.2e}")
-        assert abs(ad - fd) <= 1e-6 * max(1.0, abs(fd))
+        assert abs(ad - fd) <= 1e-8 + 1e-4 * abs(fd)
