@@ -206,9 +206,62 @@ __device__ __forceinline__ void slice_group(const double* x, int e, uint4* out /
     }
 }
 
-// grid (row groups of 8, 2 = A | B, problems); one warp per row of the operand
-// (lanes along k).  (One thread per row, which makes the loads of a transposed
-// operand coalesced, measured 2.6x slower: too few threads per operand.)
+// Strided views (a transposed operand, the right site of a merge): a block
+// takes 32 consecutive rows, lane = row and warp = a slice of the K range, so
+// that the 32 lanes of a load read 32 neighbouring rows at one k (coalesced).
+template <bool kBf16>
+__device__ void slice_rows_tiled(const OzOperand& X, int r0, int R, int K, int Kt, unsigned char* out, int* ex,
+                                 int tile, int Rt) {
+    constexpr int esize = kBf16 ? 2 : 4;
+    constexpr int G = 16 / esize;
+    constexpr int KT = kt_elems(esize);
+    __shared__ double s_mx[8][32];
+    __shared__ int s_bad[8][32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = r0 + lane;
+    const bool live = r < R;
+    double mx = 0.0;
+    int bad = 0;
+    if (live)
+        for (int k = warp; k < K; k += 8) {
+            const double v = oz_load(X, r, k);
+            mx = fmax(mx, fabs(v));
+            bad |= !isfinite(v);
+        }
+    s_mx[warp][lane] = mx;
+    s_bad[warp][lane] = bad;
+    __syncthreads();
+    for (int w = 0; w < 8; ++w) {
+        mx = fmax(mx, s_mx[w][lane]);
+        bad |= s_bad[w][lane];
+    }
+    int e = 0;
+    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    if (warp == 0) ex[r] = e;
+    const int rt = r / tile, rr = r % tile;
+    const size_t block = (size_t)tile * 64;
+    const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
+    for (int g0 = warp * G; g0 < Kt * KT; g0 += 8 * G) {
+        double x[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int k = g0 + g;
+            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
+        }
+        uint4 sl[kS];
+        slice_group<G, kBf16>(x, e, sl);
+        const int kt = g0 / KT, kk = g0 % KT;
+#pragma unroll
+        for (int t = 0; t < kS; ++t) {
+            unsigned char* blk = out + (((size_t)t * Rt + rt) * Kt + kt) * block;
+            *reinterpret_cast<uint4*>(blk + within + (size_t)(kk / G) * LBO) = sl[t];
+        }
+    }
+}
+
+// grid (row groups of 8, 2 = A | B, problems).  Views whose rows are
+// contiguous (ks == 1) take one warp per row, lanes along k; the others 32 rows
+// per block (slice_rows_tiled), the blocks past rows / 32 returning at once.
 template <bool kBf16>
 __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     constexpr int esize = kBf16 ? 2 : 4;
@@ -225,6 +278,12 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char* out = static_cast<unsigned char*>(isB ? P.bs : P.as);
     int* ex = isB ? P.eb : P.ea;
+    if (!(X.mode == 0 && X.ks == 1)) {
+        const int r0 = blockIdx.x * 32;
+        if (r0 >= Rt * tile) return;   // uniform over the block (Rt * tile is a multiple of 32)
+        slice_rows_tiled<kBf16>(X, r0, R, K, Kt, out, ex, tile, Rt);
+        return;
+    }
     const int r = blockIdx.x * 8 + warp;
     if (r >= Rt * tile) return;
     const bool live = r < R;

@@ -94,33 +94,60 @@ __global__ void __launch_bounds__(256) qrb_start_kernel(const OpDesc* descs, int
     }
 }
 
+// Reduce kMaxNb + 1 per-thread partial sums over the block in one pass: after
+// the call out[0..kMaxNb] hold the block sums (every thread may read them).
+__device__ __forceinline__ void block_sum17(double* v, double (*red)[kMaxNb + 1], double* out) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q <= kMaxNb; ++q) {
+        const double t = warp_sum(v[q]);
+        if (lane == 0) red[warp][q] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kMaxNb) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
+        out[threadIdx.x] = t;
+    }
+    __syncthreads();
+}
+
 // panel k0 of every op: window selection, factorisation with in-panel pivoting,
-// reflectors V and beta, the compact-WY T, and the panel's columns of R
+// reflectors V and beta, the compact-WY T, and the panel's columns of R.  Every
+// column's reductions (its norm, its inner products with the later panel
+// columns, their norm updates) share one block-wide reduction.
 __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* descs, int k0, int nb, int ld) {
-    extern __shared__ double P[];   // panel, column-major: P[j * mp + i]
-    __shared__ double red[kThreads / 32];
+    extern __shared__ double P[];   // panel, column-major: P[j * mp + i]; then the window's norms
+    __shared__ double red[kThreads / 32][kMaxNb + 1];
+    __shared__ double s_sum[kMaxNb + 1];
     __shared__ double s_pn[kMaxNb], s_beta[kMaxNb], s_w[kMaxNb];
     __shared__ double s_best[kThreads / 32];
     __shared__ int s_bidx[kThreads / 32];
-    __shared__ int s_piv;
+    __shared__ int s_piv, s_redo;
     const OpDesc& d = descs[blockIdx.x];
     const int m = d.m, n = d.n, r = min(m, n);
     if (k0 >= r) return;
-    const int jb = min(nb, r - k0), mp = m - k0;
+    const int jb = min(nb, r - k0), mp = m - k0, nw = n - k0;
     const Scratch s = scratch(d, ld);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    double* wn = P + (size_t)nb * ld;          // norms of logical columns k0 .. n-1 (window)
+    int* wp = reinterpret_cast<int*>(wn + ld);  // their physical columns
 
-    // 1. window: jb rounds of argmax of the norms of logical columns [k0 + t, n)
+    // 1. window: the jb largest norms among logical columns [k0, n), in order
+    for (int k = tid; k < nw; k += kThreads) {
+        wp[k] = s.perm[k0 + k];
+        wn[k] = s.cn[wp[k]];
+    }
+    __syncthreads();
     for (int t = 0; t < jb; ++t) {
         double best = -1.0;
-        int bidx = k0 + t;
-        for (int k = k0 + t + tid; k < n; k += kThreads) {
-            const double v = s.cn[s.perm[k]];
-            if (v > best) {
-                best = v;
+        int bidx = t;
+        for (int k = t + tid; k < nw; k += kThreads)
+            if (wn[k] > best) {
+                best = wn[k];
                 bidx = k;
             }
-        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const double ob = __shfl_xor_sync(0xffffffffu, best, o);
@@ -143,18 +170,22 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
                     b = s_best[w];
                     bi = s_bidx[w];
                 }
-            const int tmp = s.perm[k0 + t];
-            s.perm[k0 + t] = s.perm[bi];
-            s.perm[bi] = tmp;
+            const double tn = wn[t];
+            wn[t] = wn[bi];
+            wn[bi] = tn;
+            const int tp = wp[t];
+            wp[t] = wp[bi];
+            wp[bi] = tp;
         }
         __syncthreads();
     }
+    for (int k = tid; k < nw; k += kThreads) s.perm[k0 + k] = wp[k];
     // 2. load the panel and its norms
     for (int e = tid; e < jb * mp; e += kThreads) {
         const int j = e / mp, i = e % mp;
-        P[e] = d.Acm[(size_t)s.perm[k0 + j] * ld + k0 + i];
+        P[e] = d.Acm[(size_t)wp[j] * ld + k0 + i];
     }
-    if (tid < jb) s_pn[tid] = s.cn[s.perm[k0 + tid]];
+    if (tid < jb) s_pn[tid] = wn[tid];
     __syncthreads();
     // 3. Householder reflections with pivoting inside the panel
     for (int j = 0; j < jb; ++j) {
@@ -182,9 +213,19 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
             }
         __syncthreads();
         double* x = P + j * mp;
-        double part = 0.0;
-        for (int i = j + 1 + tid; i < mp; i += kThreads) part = fma(x[i], x[i], part);
-        const double ss = block_sum(part, red);
+        // ss = |x below row j|^2 (slot kMaxNb) and x.y_q below row j (slot q) in one reduction
+        double acc[kMaxNb + 1];
+#pragma unroll
+        for (int q = 0; q <= kMaxNb; ++q) acc[q] = 0.0;
+        for (int i = j + 1 + tid; i < mp; i += kThreads) {
+            const double xi = x[i];
+            acc[kMaxNb] = fma(xi, xi, acc[kMaxNb]);
+#pragma unroll
+            for (int q = 0; q < kMaxNb; ++q)
+                if (q > j && q < jb) acc[q] = fma(xi, P[q * mp + i], acc[q]);
+        }
+        block_sum17(acc, red, s_sum);
+        const double ss = s_sum[kMaxNb];
         const double x0 = x[j];
         const double nrm = sqrt(fma(x0, x0, ss));
         const double alpha = x0 > 0.0 ? -nrm : nrm;
@@ -195,36 +236,43 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
         double* vr = s.V + (size_t)j * ld;
         for (int i = tid; i < mp; i += kThreads) vr[i] = i < j ? 0.0 : (i == j ? v0 : x[i]);
         if (tid == 0) s_beta[j] = beta;
-        // w_q = v . y_q for the later panel columns, then y_q -= beta w_q v
-        for (int q = j + 1; q < jb; ++q) {
-            const double* y = P + q * mp;
-            double pw = 0.0;
-            for (int i = j + 1 + tid; i < mp; i += kThreads) pw = fma(x[i], y[i], pw);
-            const double w = block_sum(pw, red);
-            if (tid == 0) s_w[q] = fma(v0, y[j], w);
-        }
+        if (tid > j && tid < jb) s_w[tid] = fma(v0, P[tid * mp + j], s_sum[tid]);   // w_q = v . y_q
         __syncthreads();
         if (beta != 0.0)
-            for (int q = j + 1; q < jb; ++q) {
-                double* y = P + q * mp;
-                const double sc = beta * s_w[q];
-                for (int i = j + tid; i < mp; i += kThreads) y[i] = fma(-sc, i == j ? v0 : x[i], y[i]);
+            for (int i = j + tid; i < mp; i += kThreads) {
+                const double vi = i == j ? v0 : x[i];
+#pragma unroll
+                for (int q = 0; q < kMaxNb; ++q)
+                    if (q > j && q < jb) P[q * mp + i] = fma(-beta * s_w[q], vi, P[q * mp + i]);
             }
         __syncthreads();
         // column j of R; downdate the norms of the later panel columns
         if (tid == 0) x[j] = (ss == 0.0) ? x0 : alpha;
         for (int i = j + 1 + tid; i < mp; i += kThreads) x[i] = 0.0;
+        if (tid == 0) s_redo = 0;
         __syncthreads();
-        for (int q = j + 1; q < jb; ++q) {
-            const double* y = P + q * mp;
-            double nv = s_pn[q] - y[j] * y[j];
-            if (!(nv > 0.05 * s_pn[q])) {   // heavy cancellation: recompute below row j
-                double pr = 0.0;
-                for (int i = j + 1 + tid; i < mp; i += kThreads) pr = fma(y[i], y[i], pr);
-                nv = block_sum(pr, red);
+        if (tid > j && tid < jb) {
+            const double y = P[tid * mp + j];
+            const double nv = s_pn[tid] - y * y;
+            if (nv > 0.05 * s_pn[tid])
+                s_pn[tid] = nv;
+            else
+                s_redo = 1;   // heavy cancellation: recomputed below row j
+        }
+        __syncthreads();
+        if (s_redo) {
+#pragma unroll
+            for (int q = 0; q <= kMaxNb; ++q) acc[q] = 0.0;
+            for (int i = j + 1 + tid; i < mp; i += kThreads)
+#pragma unroll
+                for (int q = 0; q < kMaxNb; ++q)
+                    if (q > j && q < jb) acc[q] = fma(P[q * mp + i], P[q * mp + i], acc[q]);
+            block_sum17(acc, red, s_sum);
+            if (tid > j && tid < jb) {
+                const double y = P[tid * mp + j];
+                const double nv = s_pn[tid] - y * y;
+                if (!(nv > 0.05 * s_pn[tid])) s_pn[tid] = s_sum[tid];
             }
-            __syncthreads();
-            if (tid == 0) s_pn[q] = nv;
             __syncthreads();
         }
     }
@@ -247,9 +295,9 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
         }
         __syncthreads();
         if (tid < j) {
-            double acc = 0.0;
-            for (int l = tid; l < j; ++l) acc = fma(s.T[tid * kMaxNb + l], s_w[l], acc);
-            s.T[tid * kMaxNb + j] = -s_beta[j] * acc;
+            double accT = 0.0;
+            for (int l = tid; l < j; ++l) accT = fma(s.T[tid * kMaxNb + l], s_w[l], accT);
+            s.T[tid * kMaxNb + j] = -s_beta[j] * accT;
         }
         if (tid == j) s.T[j * kMaxNb + j] = s_beta[j];
         if (tid > j && tid < kMaxNb) s.T[tid * kMaxNb + j] = 0.0;
@@ -359,8 +407,16 @@ int qrb_panel_width(int chi_cap) {
     return std::max(4, std::min(kMaxNb, nb));
 }
 
+// dynamic shared memory of the panel kernel: the panel (nb x ld doubles) and
+// the window's norms and physical columns (ld doubles + ld ints)
+static size_t panel_smem(int chi_cap) {
+    const int ld = 4 * chi_cap;
+    return ((size_t)qrb_panel_width(chi_cap) * ld + ld) * sizeof(double) + (size_t)ld * sizeof(int);
+}
+
 cudaError_t qrb_prepare() {
-    return cudaFuncSetAttribute(qrb_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelBytes);
+    return cudaFuncSetAttribute(qrb_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)panel_smem(kMaxChi));
 }
 
 cudaError_t launch_qr_blocked(const OpDesc* d_desc, int nops, int chi_cap, OzProblem* probs, bool bf16,
@@ -370,7 +426,7 @@ cudaError_t launch_qr_blocked(const OpDesc* d_desc, int nops, int chi_cap, OzPro
     if (r_max <= 0 || r_max > ld) r_max = ld;
     qrb_start_kernel<<<nops, 256, 0, st>>>(d_desc, ld);
     cudaError_t e = cudaGetLastError();
-    const size_t smem = (size_t)nb * ld * sizeof(double);
+    const size_t smem = panel_smem(chi_cap);
     for (int k0 = 0; k0 < r_max && e == cudaSuccess; k0 += nb) {
         qrb_panel_kernel<<<nops, kThreads, smem, st>>>(d_desc, k0, nb, ld);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
