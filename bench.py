@@ -68,6 +68,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--probe-peaks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default Jacobi block rule")
+    ap.add_argument("--no-graph", action="store_true", help="skip the graph-replayed steps")
     ap.add_argument("--adjoint-steps", type=int, default=1,
                     help="Trotter steps of the timed gradient on the N=24 ring at chi=256 (0: skip)")
     return ap.parse_args()
@@ -524,7 +525,7 @@ def main():
     if dist:
         dist.barrier()
     arms = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
-    res = {p: run_arm(args, p, world, dist, local, graph=(p == arms[-1]),
+    res = {p: run_arm(args, p, world, dist, local, graph=(p == arms[-1] and not args.no_graph),
                       e2e_steps=(args.e2e_steps if p == arms[-1] else 0)) for p in arms}
     head = res["mixed"] if "mixed" in res else res["fp64"]
     hp = "mixed" if "mixed" in res else "fp64"

@@ -94,17 +94,19 @@ __global__ void __launch_bounds__(256) qrb_start_kernel(const OpDesc* descs, int
     }
 }
 
-// Reduce kMaxNb + 1 per-thread partial sums over the block in one pass: after
-// the call out[0..kMaxNb] hold the block sums (every thread may read them).
-__device__ __forceinline__ void block_sum17(double* v, double (*red)[kMaxNb + 1], double* out) {
+constexpr int kSums = 2 * kMaxNb + 1;   // per column: x . y_q (q > j), |x|^2, v_t . v_j (t < j)
+
+// Reduce kSums per-thread partial sums over the block in one pass: after the
+// call out[0..kSums) hold the block sums (every thread may read them).
+__device__ __forceinline__ void block_sums(double* v, double (*red)[kSums], double* out) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int q = 0; q <= kMaxNb; ++q) {
+    for (int q = 0; q < kSums; ++q) {
         const double t = warp_sum(v[q]);
         if (lane == 0) red[warp][q] = t;
     }
     __syncthreads();
-    if (threadIdx.x <= kMaxNb) {
+    if (threadIdx.x < kSums) {
         double t = 0.0;
 #pragma unroll
         for (int w = 0; w < kThreads / 32; ++w) t += red[w][threadIdx.x];
@@ -119,9 +121,9 @@ __device__ __forceinline__ void block_sum17(double* v, double (*red)[kMaxNb + 1]
 // columns, their norm updates) share one block-wide reduction.
 __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* descs, int k0, int nb, int ld) {
     extern __shared__ double P[];   // panel, column-major: P[j * mp + i]; then the window's norms
-    __shared__ double red[kThreads / 32][kMaxNb + 1];
-    __shared__ double s_sum[kMaxNb + 1];
-    __shared__ double s_pn[kMaxNb], s_beta[kMaxNb], s_w[kMaxNb];
+    __shared__ double red[kThreads / 32][kSums];
+    __shared__ double s_sum[kSums];
+    __shared__ double s_pn[kMaxNb], s_beta[kMaxNb], s_w[kMaxNb], s_z[kMaxNb];
     __shared__ double s_best[kThreads / 32];
     __shared__ int s_bidx[kThreads / 32];
     __shared__ int s_piv, s_redo;
@@ -213,18 +215,23 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
             }
         __syncthreads();
         double* x = P + j * mp;
-        // ss = |x below row j|^2 (slot kMaxNb) and x.y_q below row j (slot q) in one reduction
-        double acc[kMaxNb + 1];
+        // one reduction: x.y_q below row j (slot q > j), |x below row j|^2 (slot
+        // kMaxNb) and, for T, x.v_t below row j (slot kMaxNb + 1 + t, t < j; the
+        // earlier reflectors are read back from V); v_t . v_j then follows from
+        // v_j = (v0 at row j, x below)
+        double acc[kSums];
 #pragma unroll
-        for (int q = 0; q <= kMaxNb; ++q) acc[q] = 0.0;
+        for (int q = 0; q < kSums; ++q) acc[q] = 0.0;
         for (int i = j + 1 + tid; i < mp; i += kThreads) {
             const double xi = x[i];
             acc[kMaxNb] = fma(xi, xi, acc[kMaxNb]);
 #pragma unroll
-            for (int q = 0; q < kMaxNb; ++q)
+            for (int q = 0; q < kMaxNb; ++q) {
                 if (q > j && q < jb) acc[q] = fma(xi, P[q * mp + i], acc[q]);
+                if (q < j) acc[kMaxNb + 1 + q] = fma(xi, s.V[(size_t)q * ld + i], acc[kMaxNb + 1 + q]);
+            }
         }
-        block_sum17(acc, red, s_sum);
+        block_sums(acc, red, s_sum);
         const double ss = s_sum[kMaxNb];
         const double x0 = x[j];
         const double nrm = sqrt(fma(x0, x0, ss));
@@ -237,7 +244,17 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
         for (int i = tid; i < mp; i += kThreads) vr[i] = i < j ? 0.0 : (i == j ? v0 : x[i]);
         if (tid == 0) s_beta[j] = beta;
         if (tid > j && tid < jb) s_w[tid] = fma(v0, P[tid * mp + j], s_sum[tid]);   // w_q = v . y_q
+        // T column j: z_t = v_t . v_j = v_t[j] v0 + (x . v_t below row j), then
+        // T[t][j] = -beta_j sum_{t <= l < j} T[t][l] z_l, T[j][j] = beta_j
+        if (tid < j) s_z[tid] = fma(s.V[(size_t)tid * ld + j], v0, s_sum[kMaxNb + 1 + tid]);
         __syncthreads();
+        if (tid < j) {
+            double accT = 0.0;
+            for (int l = tid; l < j; ++l) accT = fma(s.T[tid * kMaxNb + l], s_z[l], accT);
+            s.T[tid * kMaxNb + j] = -beta * accT;
+        }
+        if (tid == j) s.T[j * kMaxNb + j] = beta;
+        if (tid > j && tid < kMaxNb) s.T[tid * kMaxNb + j] = 0.0;
         if (beta != 0.0)
             for (int i = j + tid; i < mp; i += kThreads) {
                 const double vi = i == j ? v0 : x[i];
@@ -262,12 +279,12 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
         __syncthreads();
         if (s_redo) {
 #pragma unroll
-            for (int q = 0; q <= kMaxNb; ++q) acc[q] = 0.0;
+            for (int q = 0; q < kSums; ++q) acc[q] = 0.0;
             for (int i = j + 1 + tid; i < mp; i += kThreads)
 #pragma unroll
                 for (int q = 0; q < kMaxNb; ++q)
                     if (q > j && q < jb) acc[q] = fma(P[q * mp + i], P[q * mp + i], acc[q]);
-            block_sum17(acc, red, s_sum);
+            block_sums(acc, red, s_sum);
             if (tid > j && tid < jb) {
                 const double y = P[tid * mp + j];
                 const double nv = s_pn[tid] - y * y;
@@ -280,28 +297,6 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
     for (int e = tid; e < jb * mp; e += kThreads) {
         const int j = e / mp, i = e % mp;
         d.Acm[(size_t)s.perm[k0 + j] * ld + k0 + i] = P[e];
-    }
-    // 5. T: T[j][j] = beta_j, T[0:j, j] = -beta_j T[0:j, 0:j] (V_{0:j} v_j)
-    __syncthreads();
-    for (int j = 0; j < jb; ++j) {
-        // z_t = v_t . v_j for t < j, one warp per t
-        for (int t = warp; t < j; t += kThreads / 32) {
-            const double* a = s.V + (size_t)t * ld;
-            const double* b = s.V + (size_t)j * ld;
-            double z = 0.0;
-            for (int i = lane; i < mp; i += 32) z = fma(a[i], b[i], z);
-            z = warp_sum(z);
-            if (lane == 0) s_w[t] = z;
-        }
-        __syncthreads();
-        if (tid < j) {
-            double accT = 0.0;
-            for (int l = tid; l < j; ++l) accT = fma(s.T[tid * kMaxNb + l], s_w[l], accT);
-            s.T[tid * kMaxNb + j] = -s_beta[j] * accT;
-        }
-        if (tid == j) s.T[j * kMaxNb + j] = s_beta[j];
-        if (tid > j && tid < kMaxNb) s.T[tid * kMaxNb + j] = 0.0;
-        __syncthreads();
     }
 }
 
