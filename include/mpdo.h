@@ -81,6 +81,9 @@ typedef struct {
     unsigned barrier_timeout_ms;  /* limit of every device-side wait (default 4000) */
     int max_slots;           /* <= 0: automatic; else max two-site ops in flight */
     int device;              /* CUDA device ordinal; < 0: the calling thread's current device */
+    int qr_blocked;          /* mixed path only: 1 = blocked Householder QR (window-pivoted panels of
+                                16 columns, trailing updates on the tensor cores); 0 (default) =
+                                the column-by-column QR, measured faster on this GPU */
 } mpdo_config;
 
 typedef struct {
@@ -245,7 +248,7 @@ int mpdo_inject_fault(mpdo_ctx *ctx, int kind);
  * kernel kind k (0 merge+gate, 1 Jacobi SVD (FP64), 2 truncate, 3 reconstruct,
  * 4 trace, 5 environments/measure, 6 gate build, 7 FP32 preconditioning
  * Jacobi, 8 preconditioner GEMMs, 9 Householder QR), the device time in ms,
- * the number of launches and the algorithmic flops of the work launched
+ * the number of kernels launched and the algorithmic flops of the work launched
  * (merge 32 cl cm cr, gate 512 cl cr, SVD 21 n^3 with n = 4 max(cl, cr),
  * reconstruct 32 cl cr k; 0 for the other kinds).  mpdo_profile_read copies
  * up to kmax kinds (any pointer may be NULL) and, if reset != 0, zeroes them. */

@@ -149,13 +149,13 @@ int alloc_slots(mpdo_ctx* c, int want) {
 
 namespace mpdo {
 
-void prof_collect(mpdo_ctx* c, int k, double flops) {
+void prof_collect(mpdo_ctx* c, int k, double flops, int kernels) {
     if (!c->prof) return;
     float ms = 0.0f;
     if (cudaEventSynchronize(c->ev[2 * k + 1]) == cudaSuccess &&
         cudaEventElapsedTime(&ms, c->ev[2 * k], c->ev[2 * k + 1]) == cudaSuccess)
         c->prof_ms[k] += ms;
-    c->prof_launch[k] += 1;
+    c->prof_launch[k] += kernels;
     c->prof_flops[k] += flops;
 }
 
@@ -349,6 +349,7 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
 
     const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), c->slots);
     double qr_flops_chunk = 0.0;
+    int qr_kernels_chunk = 1;
     // Jacobi launch plan: share the co-resident CTAs among the ops in
     // proportion to their work; h_cta/d_cta hold [op of each CTA | rank | CTAs per op]
     auto plan = [&](bool fp32, int* hbase, int& total) -> int {
@@ -416,13 +417,14 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
             fl_qr += 4.0 * d.m * d.n * d.c - 2.0 * (d.m + d.n) * d.c * d.c + 4.0 / 3.0 * d.c * d.c * d.c;
         }
         qr_flops_chunk = fl_qr;
-        if (c->mixed && qrb_fits(cap)) {
+        if (c->mixed && c->cfg.qr_blocked && qrb_fits(cap)) {
             // mixed path: blocked QR, trailing updates on the tensor cores
             int r_max = 1;
             for (int s = 0; s < nops; ++s) r_max = std::max(r_max, c->h_desc[s].c);
             ProfScope p_qr(c, K_QR);
             CU(launch_qr_blocked(c->d_desc, nops, cap, c->d_oz, c->oz_bf16, timeout_ns, c->st, r_max));
             p_qr.stop();
+            qr_kernels_chunk = qrb_kernels(cap, r_max);
         } else {
             CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
             CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
@@ -489,15 +491,17 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         const OpDesc& d = c->h_desc[s];
         fl_rec += 32.0 * d.cl * d.cr * c->h_dims[(size_t)d.b * (N + 1) + c->layers[items[s].layer][items[s].idx].p + 1];
     }
-    prof_collect(c, K_MERGE, fl_merge);
-    prof_collect(c, K_QR, qr_flops_chunk);
-    prof_collect(c, K_JACOBI, fl_svd);
+    // kernels per stage: a tensor-core product is three (operand set-up,
+    // slicing, slice products), the merge adds the gate/weight kernel
+    prof_collect(c, K_MERGE, fl_merge, c->mixed ? 4 : 1);
+    prof_collect(c, K_QR, qr_flops_chunk, qr_kernels_chunk);
+    prof_collect(c, K_JACOBI, fl_svd, 1);
     if (c->mixed) {
-        prof_collect(c, K_JACOBI32, 0.0);
-        prof_collect(c, K_GEMM, fl_gemm);
+        prof_collect(c, K_JACOBI32, 0.0, 1);
+        prof_collect(c, K_GEMM, fl_gemm, 9);
     }
-    prof_collect(c, K_TRUNC, 0.0);
-    prof_collect(c, K_RECON, fl_rec);
+    prof_collect(c, K_TRUNC, 0.0, 1);
+    prof_collect(c, K_RECON, fl_rec, c->mixed ? 3 : 1);
     for (int s = 0; s < nops && log_ranks; ++s) {
         const Item& it = items[s];
         const Op& op = c->layers[it.layer][it.idx];
@@ -513,7 +517,7 @@ int normalize_trace(mpdo_ctx* c) {
     CU(launch_trace_normalize(c->d_sites, sites_f32(c), c->d_dims, c->N, c->B, c->cap, c->cfg.force_trace, c->d_trace,
                               c->d_status, c->st));
     p_trace.stop();
-    prof_collect(c, K_TRACE, 0.0);
+    prof_collect(c, K_TRACE, 0.0, 1);
     return MPDO_OK;
 }
 

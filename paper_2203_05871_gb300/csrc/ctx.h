@@ -167,7 +167,9 @@ struct ProfScope {
         if (c->prof) cudaEventRecord(c->ev[2 * k + 1], c->st);
     }
 };
-void prof_collect(mpdo_ctx* c, int k, double flops);
+// adds the time between the events of kind k, the kernels launched between
+// them and their algorithmic flops to the profile
+void prof_collect(mpdo_ctx* c, int k, double flops, int kernels);
 
 // Jacobi rows per block of a (chi_l, chi_r) class: the autotuned value, else dflt.
 inline int tuned_block_rows(const mpdo_ctx* c, int cl, int cr, bool fp32, int dflt) {

@@ -180,7 +180,7 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
             }
             const size_t sync_bytes = sizeof(unsigned) * jacobi_sync_words_per_op() * nops;
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
-            if (c->mixed && qrb_fits(cap))
+            if (c->mixed && c->cfg.qr_blocked && qrb_fits(cap))
                 CU(launch_qr_blocked(ch.d_desc, nops, cap, c->d_oz, c->oz_bf16, timeout_ns, st, 0));
             else
                 CU(launch_qr(ch.d_desc, ch.d_ctaqr, ch.d_ctaqr + g->Rq, ch.d_ctaqr + 2 * g->Rq, c->d_sync, g->Rq,

@@ -223,6 +223,8 @@ cudaError_t launch_gate_weight(const OpDesc* d_desc, int nops, int chi_cap, cuda
 // reflectors and products), d.snorm (column norms, permutation), the op's slice
 // buffers.  One panel loop over the chunk (ops with fewer columns idle through it).
 int qrb_panel_width(int chi_cap);
+// kernels one launch_qr_blocked issues for ranks up to r_max
+int qrb_kernels(int chi_cap, int r_max);
 // the blocked QR needs d.W to hold its scratch (48 ld + 256 doubles of ld^2)
 inline bool qrb_fits(int chi_cap) { return 4 * chi_cap >= 128; }
 cudaError_t qrb_prepare();

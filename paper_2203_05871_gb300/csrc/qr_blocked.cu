@@ -66,19 +66,6 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// sum over the block of v (every thread returns it); red: >= 16 doubles of shared memory
-__device__ double block_sum(double v, double* red) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    v = warp_sum(v);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-    return t;
-}
-
 // identity permutation and squared column norms of the whole matrix
 __global__ void __launch_bounds__(256) qrb_start_kernel(const OpDesc* descs, int ld) {
     const OpDesc& d = descs[blockIdx.x];
@@ -412,6 +399,14 @@ static size_t panel_smem(int chi_cap) {
 cudaError_t qrb_prepare() {
     return cudaFuncSetAttribute(qrb_panel_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)panel_smem(kMaxChi));
+}
+
+int qrb_kernels(int chi_cap, int r_max) {
+    const int ld = 4 * chi_cap, nb = qrb_panel_width(chi_cap);
+    if (r_max <= 0 || r_max > ld) r_max = ld;
+    // start and finish, and per panel: the panel, two operand set-ups, two
+    // products (slicing + slice products each), W^T and the norms
+    return 2 + ((r_max + nb - 1) / nb) * 9;
 }
 
 cudaError_t launch_qr_blocked(const OpDesc* d_desc, int nops, int chi_cap, OzProblem* probs, bool bf16,

@@ -215,11 +215,14 @@ def test_mixed_chain8_forty_steps(kind):
     assert worst <= TOL_MIXED
 
 
+# qr "blocked": the opt-in blocked Householder QR of the preconditioner
+# (panels of 16 columns, trailing updates as tensor-core slice products)
+@pytest.mark.parametrize("qr", ["column", "blocked"])
 @pytest.mark.parametrize("kind", ["tf32", "bf16"])
 @pytest.mark.parametrize("bonds,n", [(W.ring_bonds(8), 8), (W.grid_snake_bonds(3, 3), 9)])
-def test_mixed_swap_routed(bonds, n, kind):
+def test_mixed_swap_routed(bonds, n, kind, qr):
     wl = W.random_model(n, bonds, 57, chi_max=32, cutoff=1e-11, dt=0.05)
-    s = solver_for(wl, precision=_mixed(kind))
+    s = solver_for(wl, precision=_mixed(kind), qr_blocked=(qr == "blocked"))
     compare_to_oracle(wl, 3, s, tol=TOL_MIXED)
 
 
@@ -235,13 +238,14 @@ def test_mixed_batched_uneven_chi():
 # and the kept subspace turns by (perturbation / gap): the contractions and the
 # preconditioner products must be FP64-class (the tensor-core slice products
 # are) for the mixed tolerance to hold there.
+@pytest.mark.parametrize("qr", ["column", "blocked"])
 @pytest.mark.parametrize("kind", ["tf32", "bf16"])
 @pytest.mark.parametrize("decay,tol", [(0.0, TOL_MIXED), (0.045, TOL_MIXED)])
-def test_mixed_chi256_one_step_sampled(decay, tol, kind):
+def test_mixed_chi256_one_step_sampled(decay, tol, kind, qr):
     n = 10
     wl = W.uniform_model("chain10_chi256", n, W.chain_bonds(n), chi_max=256, cutoff=1e-10, dt=0.02)
     dims, tens = W.random_mpo_state(n, 256, seed=11, decay=decay)
-    s = solver_for(wl, chi_cap=256, precision=_mixed(kind))
+    s = solver_for(wl, chi_cap=256, precision=_mixed(kind), qr_blocked=(qr == "blocked"))
     s.set_state(0, dims, tens)
     s.step(1)
     log = [int(k) for k in s.rank_log(1)[0]]
@@ -257,7 +261,7 @@ def test_mixed_chi256_one_step_sampled(decay, tol, kind):
     scale = np.array([abs(o.state.expect_2q(i, j)) + abs(rz[i] * rz[j]) for (i, j) in pairs])
     ez = np.abs(gz - rz) / np.maximum(1.0, np.abs(rz))
     ezz = np.abs(g - rg) / np.maximum(1.0, scale)
-    print(f"mixed {kind} chi256 decay {decay}: max rel |dZ| = {ez.max():.2e}, |dZZc| = {ezz.max():.2e}")
+    print(f"mixed {kind} {qr} QR chi256 decay {decay}: max rel |dZ| = {ez.max():.2e}, |dZZc| = {ezz.max():.2e}")
     assert np.all(ez <= tol) and np.all(ezz <= tol)
     md = s.status()["max_discarded"][0]
     assert o.max_discarded > 0.0 and abs(md - o.max_discarded) <= tol * o.max_discarded
