@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--probe-peaks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default Jacobi block rule")
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replayed steps")
+    ap.add_argument("--no-observables", action="store_true",
+                    help="skip the observables timing on the 4x10 snake at chi 512")
     ap.add_argument("--qr-blocked", action="store_true",
                     help="mixed path: blocked Householder QR (tensor-core trailing updates) instead of the column QR")
     ap.add_argument("--adjoint-steps", type=int, default=1,
@@ -94,6 +96,11 @@ def make_workload(name):
         states = [W.random_mpo_state(wl.n, int(wl.chi_max[b]), seed=2203058712 + 100 + b, decay=DECAY)
                   for b in range(wl.batch)]
         return wl, states, 256
+    if name == "snake4x10_chi512":
+        # the 4x10 grid on a snake path at its chi_max = 512 (bond ranges 1, 3,
+        # 5, 7 through swap chains), started at saturated chi
+        wl = W.grid4x10_snake()
+        return wl, [W.random_mpo_state(wl.n, 512, seed=2203058712 + 3, decay=DECAY)], 512
     table = {"chain20_chi256": (256, DECAY), "chain20_chi256_flat": (256, 0.0),
              "chain20_chi128": (128, DECAY), "chain20_chi64": (64, DECAY),
              "chain10_chi256": (256, DECAY)}
@@ -417,6 +424,73 @@ def qr_roofline(prof):
             "note": "flops 4 m n r - 2 (m + n) r^2 + 4/3 r^3 per op (r = min(m, n)); peak = nominal FP64"}
 
 
+def run_observables(args, local, reps=5):
+    """Measurement (a12) and the global quantities on the 4x10 snake at
+    chi_max = 512 (N = 40, bonds saturated from position 4 inward, seeded
+    random MPO): every <Z_i>, every connected <Z_i Z_j> (780 pairs), S2 and the
+    central OSEE, each timed with CUDA events on the solver's stream after
+    warm-up.  The sites (336 MB) exceed L2, so no flush is needed."""
+    import numpy as np
+    import torch
+    import workloads as W
+    from paper_2203_05871_gb300 import FP64, Solver
+
+    wl = W.grid4x10_snake()
+    n, chi = wl.n, 512
+    dims, tens = W.random_mpo_state(n, chi, seed=2203058712 + 3, decay=DECAY)
+    stream = torch.cuda.Stream()
+    s = Solver(n, batch=1, chi_cap=chi, stream=stream, precision=FP64, max_slots=1)
+    s.build_gates(wl)
+    s.set_state(0, dims, tens)
+    pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    o1 = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    o2 = torch.empty((1, len(pairs)), dtype=torch.float64, device="cuda")
+    calls = {"z_all": lambda: s.measure_1q(range(n), "Z", out=o1),
+             "zz_connected_all_pairs": lambda: s.measure_2q(pairs, "ZZ", connected=True, out=o2),
+             "renyi2": lambda: s.renyi2(),
+             "osee_central": lambda: s.osee()}
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, fn in calls.items():
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"ms": a.elapsed_time(b) / reps}
+    d = np.asarray(dims, dtype=np.float64)
+    slice_bytes = float(np.sum(d[:-1] * d[1:])) * 8.0        # one Pauli slice of every site
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    # <Z_i> for all i: left and right I-environments and one Z slice per site
+    b1 = 3.0 * slice_bytes
+    res["z_all"]["roofline"] = {"bound": "hbm", "algorithmic_bytes": b1,
+                                "achieved": b1 / (res["z_all"]["ms"] * 1e-3) / 1e9,
+                                "peak": hbm, "unit": "GB/s"}
+    # all pairs: the I and Z slices once each beyond the environments
+    # (the stacked form); FP64 flops of the stacked propagation, sum over j of
+    # (rows alive) x 2 slices x chi_j chi_j+1 FMA
+    b2 = 4.0 * slice_bytes
+    fl2 = sum(4.0 * j * d[j] * d[j + 1] for j in range(n))
+    res["zz_connected_all_pairs"]["roofline"] = {
+        "bound": "hbm", "algorithmic_bytes": b2, "achieved": b2 / (res["zz_connected_all_pairs"]["ms"] * 1e-3) / 1e9,
+        "peak": hbm, "unit": "GB/s", "fp64_flops": fl2,
+        "fp64_tflops": fl2 / (res["zz_connected_all_pairs"]["ms"] * 1e-3) / 1e12}
+    for k in ("z_all", "zz_connected_all_pairs"):
+        r = res[k]["roofline"]
+        r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
+    return {"workload": "snake4x10_chi512 (4x10 grid on a snake path, N = 40, chi 512, seeded random MPO, "
+                        "Schmidt grading exp(-%.3f r)), FP64 storage" % DECAY,
+            "reps": reps, "calls": res, "clocks": clk.summary(),
+            "note": "algorithmic bytes: one Pauli slice of every site = sum_p chi_p chi_p+1 x 8 B; "
+                    "<Z> reads three (two environments, the Z slice), all pairs four (+ the I slice "
+                    "propagated); peak = measured HBM copy bandwidth"}
+
+
 def run_adjoint(args, local):
     """One gradient (checkpointed forward + backward) of sum_i zbar_i <z_i> +
     sum_{i<j} wbar_ij conn_ij on the N=24 ring (closing bond routed by swaps)
@@ -599,6 +673,11 @@ def main():
         line["batched"] = bs
     if args.adjoint_steps > 0:
         line["adjoint"] = run_adjoint(args, local)
+    if not args.no_observables:
+        try:
+            line["observables"] = run_observables(args, local)
+        except Exception as exc:   # keep the headline line; report what failed
+            line["observables"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline_subprocess(args, "lapack", args.cpu_ops, 1)
         if not args.no_cpu_plain:

@@ -50,7 +50,8 @@ void free_all(mpdo_ctx* c) {
     release_slots(c);
     void* ptrs[] = {c->d_sites, c->d_lam,  c->d_dims,  c->d_status, c->d_maxdisc, c->d_trace, c->d_params,
                     c->d_gates, c->d_specs, c->d_envL,  c->d_envR,   c->d_full,    c->d_one_a, c->d_one_b,
-                    c->d_out,   c->d_q,     c->d_pairs, c->d_need,   c->d_jb_table, c->d_gq};
+                    c->d_out,   c->d_q,     c->d_pairs, c->d_need,   c->d_jb_table, c->d_gq,
+                    c->d_wstack, c->d_part};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& e : c->ev)
@@ -641,6 +642,8 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
         (e = dalloc(&c->d_envL, (size_t)B * (N + 1) * c->cap)) != cudaSuccess ||
         (e = dalloc(&c->d_envR, (size_t)B * (N + 1) * c->cap)) != cudaSuccess ||
         (e = dalloc(&c->d_full, (size_t)B * N * N)) != cudaSuccess ||
+        (e = dalloc(&c->d_wstack, two_stack_doubles(N, B, c->cap))) != cudaSuccess ||
+        (e = dalloc(&c->d_part, two_part_doubles(N, B, c->cap))) != cudaSuccess ||
         (e = dalloc(&c->d_one_a, (size_t)B * N * 4)) != cudaSuccess ||
         (e = dalloc(&c->d_one_b, (size_t)B * N)) != cudaSuccess ||
         (e = dalloc(&c->d_out, (size_t)B * N * N)) != cudaSuccess ||
@@ -978,7 +981,7 @@ int mpdo_measure_2q(mpdo_ctx* c, const int* pairs, int np, const char comp[2], i
         const int x = pass == 0 ? ca : cb, y = pass == 0 ? cb : ca;
         CU(cudaMemcpyAsync(c->d_need, need.data(), N, cudaMemcpyHostToDevice, c->st));
         CU(launch_measure_2q(c->d_sites, sites_f32(c), c->d_dims, N, B, c->cap, c->d_envL, c->d_envR, x, y, c->d_need,
-                             c->d_full, c->st));
+                             c->d_wstack, c->d_part, c->d_full, c->st));
         CU(cudaMemcpyAsync(c->d_pairs, trip.data(), sizeof(int) * trip.size(), cudaMemcpyHostToDevice, c->st));
         const double* oa = pass == 0 ? c->d_one_a : c->d_one_b;
         const double* ob = pass == 0 ? c->d_one_b : c->d_one_a;

@@ -108,6 +108,7 @@ struct mpdo_ctx {
     int jacobi_resident = 0;
     int qr_resident = 0;
     // measurement
+    double *d_wstack = nullptr, *d_part = nullptr;   // all-pairs propagation scratch
     double *d_envL = nullptr, *d_envR = nullptr, *d_full = nullptr, *d_one_a = nullptr, *d_one_b = nullptr,
            *d_out = nullptr;
     int *d_q = nullptr, *d_pairs = nullptr;

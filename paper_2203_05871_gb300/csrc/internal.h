@@ -265,11 +265,15 @@ cudaError_t launch_environments(const void* sites, int sites_f32, const int* dim
 cudaError_t launch_measure_1q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                               const double* envL, const double* envR, const int* d_q, int nq,
                               int comp, double* out, cudaStream_t st);
-// all-pairs propagation: for each (b, i) computes E(ca at i, cb at j) for j > i
-// into full[b][i][j]; unused entries untouched.
+// all-pairs propagation: E(ca at i, cb at j) / E0 for every i with need[i] and
+// every j > i into full[b][i][j]; unused entries untouched.  Scratch: wstack
+// (two_stack_doubles) and part (two_part_doubles), device.
+size_t two_stack_doubles(int n, int B, int chi_cap);
+size_t two_part_doubles(int n, int B, int chi_cap);
 cudaError_t launch_measure_2q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                               const double* envL, const double* envR, int ca, int cb,
-                              const unsigned char* d_need_i, double* full, cudaStream_t st);
+                              const unsigned char* d_need_i, double* wstack, double* part, double* full,
+                              cudaStream_t st);
 // d_trip[m][3] = (i, j, k): out[b][k] = full[b][i][j] (- one_a[b][i] one_b[b][j] if connected)
 cudaError_t launch_gather_2q(const double* full, const double* one_a, const double* one_b,
                              const int* d_trip, int m, int np, int n, int B, int connected,

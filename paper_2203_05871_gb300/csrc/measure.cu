@@ -75,38 +75,53 @@ __global__ void __launch_bounds__(MT) trace_kernel(void* sites, int f32, const i
     }
 }
 
-// blockIdx.y == 0: left environments, 1: right environments
-__global__ void __launch_bounds__(MT) env_kernel(const void* sites, int f32, const int* dims, int n, int cap,
-                                                 double* envL, double* envR) {
-    const int b = blockIdx.x;
+// One step t of both environments, spread over CTAs (a single CTA per
+// environment would leave all but two SMs idle and run at one SM's FP64 rate):
+//   blockIdx.y == 0: L_{t+1} = L_t B_t[I], EW columns of L_{t+1} per CTA;
+//   blockIdx.y == 1: R_p = B_p[I] R_{p+1} with p = n - 1 - t, EW entries per CTA.
+// Step 0 uses L_0 = R_n = (1) and also stores them for the readers.
+constexpr int EW = 16;
+__global__ void __launch_bounds__(256) env_step_kernel(const void* sites, int f32, const int* dims, int n, int cap,
+                                                       int t, double* envL, double* envR) {
+    const int b = blockIdx.z;
     const int* dm = dims + (size_t)b * (n + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.y == 0) {
+        const int p = t, cl = dm[p], cr = dm[p + 1];
+        const int r0 = blockIdx.x * EW;
         double* E = envL + (size_t)b * (n + 1) * cap;
-        if (threadIdx.x == 0) E[0] = 1.0;
+        if (p == 0 && blockIdx.x == 0 && threadIdx.x == 0) E[0] = 1.0;
+        if (r0 >= cr) return;
+        const SiteRef S = site_ptr(sites, f32, b, p, n, cap);
+        const double* vin = E + (size_t)p * cap;
+        const int c = threadIdx.x % EW, g = threadIdx.x / EW;   // column, row group (16 groups)
+        const int r = r0 + c;
+        double acc = 0.0;
+        if (r < cr)
+            for (int l = g; l < cl; l += 256 / EW) acc = fma(p == 0 ? 1.0 : vin[l], S[((size_t)l * 4) * cap + r], acc);
+        __shared__ double red[256];
+        red[threadIdx.x] = acc;
         __syncthreads();
-        for (int p = 0; p < n; ++p) {
-            vec_slice(site_ptr(sites, f32, b, p, n, cap), 0, dm[p], dm[p + 1], cap, E + (size_t)p * cap,
-                      E + (size_t)(p + 1) * cap);
-            __syncthreads();
+        if (g == 0 && r < cr) {
+            double sum = 0.0;
+            for (int k = 0; k < 256 / EW; ++k) sum += red[k * EW + c];
+            E[(size_t)(p + 1) * cap + r] = sum;
         }
     } else {
+        const int p = n - 1 - t, cl = dm[p], cr = dm[p + 1];
+        const int l0 = blockIdx.x * EW;
         double* E = envR + (size_t)b * (n + 1) * cap;
-        if (threadIdx.x == 0) E[(size_t)n * cap] = 1.0;
-        __syncthreads();
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int p = n - 1; p >= 0; --p) {
-            const SiteRef S = site_ptr(sites, f32, b, p, n, cap);
-            const double* rin = E + (size_t)(p + 1) * cap;
-            double* rout = E + (size_t)p * cap;
-            const int cl = dm[p], cr = dm[p + 1];
-            for (int l = warp; l < cl; l += nw) {
-                double acc = 0.0;
-                for (int r = lane; r < cr; r += 32) acc = fma(S[((size_t)l * 4) * cap + r], rin[r], acc);
+        if (p == n - 1 && blockIdx.x == 0 && threadIdx.x == 0) E[(size_t)n * cap] = 1.0;
+        if (l0 >= cl) return;
+        const SiteRef S = site_ptr(sites, f32, b, p, n, cap);
+        const double* rin = E + (size_t)(p + 1) * cap;
+        const int lend = min(l0 + EW, cl);
+        for (int l = l0 + warp; l < lend; l += 8) {
+            double acc = 0.0;
+            for (int r = lane; r < cr; r += 32) acc = fma(S[((size_t)l * 4) * cap + r], p == n - 1 ? 1.0 : rin[r], acc);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-                if (lane == 0) rout[l] = acc;
-            }
-            __syncthreads();
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) E[(size_t)p * cap + l] = acc;
         }
     }
 }
@@ -147,43 +162,101 @@ __global__ void __launch_bounds__(MT) one_kernel(const void* sites, int f32, con
     if (threadIdx.x == 0) out[(size_t)b * nq + k] = tot / E0;
 }
 
-// for each (b, i) with need[i]: w = L_i B_i[ca]; for j > i:
-// full[b][i][j] = (w B_j[cb]) . R_{j+1} / E0 ;  w <- w B_j[I]
-__global__ void __launch_bounds__(MT) two_kernel(const void* sites, int f32, const int* dims, int n, int cap,
-                                                 const double* envL, const double* envR, int ca, int cb,
-                                                 const unsigned char* need, double* full) {
-    const int i = blockIdx.x, b = blockIdx.y;
-    if (!need[i] || i >= n - 1) return;
+// All-pairs two-point values as one stacked propagation over j (the rows
+// w_i for every i < j advance together, so site j's slices are read once per
+// j instead of once per (i, j)).  Step j, per instance b and per tile of TW
+// columns r of bond j+1:
+//   for i < j with need[i]:  x = w_i B_j[cb],  part[b][j][tile][i] = x . R_{j+1}
+//                            (over the tile's columns),  w_i <- w_i B_j[I]
+//   if need[j] (j < n-1):    w_j = L_j B_j[ca]   (the row starts here)
+// w lives in win (read) and wout (written), [b][n][cap] each, swapped per
+// step.  The tile's three slices are staged in shared memory ([l][TW] each);
+// a warp takes one row i at a time, its lanes split l.  The sum over tiles
+// (two_reduce_kernel) keeps the result independent of the launch shape.
+constexpr int TW = 4;
+__global__ void __launch_bounds__(256) two_stack_kernel(const void* sites, int f32, const int* dims, int n, int cap,
+                                                        const double* envL, const double* envR, int ca, int cb,
+                                                        const unsigned char* need, int j, const double* win,
+                                                        double* wout, double* part, int ntiles) {
+    const int b = blockIdx.y, tile = blockIdx.x;
     const int* dm = dims + (size_t)b * (n + 1);
-    const double E0 = envL[((size_t)b * (n + 1) + n) * cap];
-    __shared__ double w0[kMaxChi], w1[kMaxChi];
-    const double* Li = envL + ((size_t)b * (n + 1) + i) * cap;
-    vec_slice(site_ptr(sites, f32, b, i, n, cap), ca, dm[i], dm[i + 1], cap, Li, w0);
-    __syncthreads();
-    double* w = w0;
-    double* wn = w1;
-    for (int j = i + 1; j < n; ++j) {
-        const SiteRef S = site_ptr(sites, f32, b, j, n, cap);
-        const double* Rj = envR + ((size_t)b * (n + 1) + j + 1) * cap;
-        const int cl = dm[j], cr = dm[j + 1];
-        double part = 0.0;
-        for (int r = threadIdx.x; r < cr; r += blockDim.x) {
-            double acc = 0.0, accI = 0.0;
-            for (int l = 0; l < cl; ++l) {
-                const double wl = w[l];
-                acc = fma(wl, S[((size_t)l * 4 + cb) * cap + r], acc);
-                accI = fma(wl, S[((size_t)l * 4) * cap + r], accI);
-            }
-            part = fma(acc, Rj[r], part);
-            wn[r] = accI;
-        }
-        const double tot = block_sum(part);
-        if (threadIdx.x == 0) full[((size_t)b * n + i) * n + j] = tot / E0;
-        __syncthreads();
-        double* t = w;
-        w = wn;
-        wn = t;
+    const int cl = dm[j], cr = dm[j + 1];
+    const int r0 = tile * TW;
+    if (r0 >= cr) return;
+    extern __shared__ double sm[];
+    double* sI = sm;                     // [cap][TW]: slice I of site j, the tile's columns
+    double* sB = sm + (size_t)cap * TW;  // slice cb
+    double* sA = sB + (size_t)cap * TW;  // slice ca
+    const SiteRef S = site_ptr(sites, f32, b, j, n, cap);
+    for (int e = threadIdx.x; e < cl * TW; e += blockDim.x) {
+        const int l = e / TW, c = e % TW, r = r0 + c;
+        const bool in = r < cr;
+        const size_t base = (size_t)l * 4 * cap + r;
+        sI[e] = in ? S[base] : 0.0;
+        sB[e] = in ? S[base + (size_t)cb * cap] : 0.0;
+        sA[e] = in ? S[base + (size_t)ca * cap] : 0.0;
     }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double* Lj = envL + ((size_t)b * (n + 1) + j) * cap;
+    const double* Rn = envR + ((size_t)b * (n + 1) + j + 1) * cap;
+    const double* W = win + (size_t)b * n * cap;
+    double* Wn = wout + (size_t)b * n * cap;
+    for (int i = warp; i <= j; i += 8) {
+        if (!need[i] || (i == j && j >= n - 1)) continue;
+        const bool seed = i == j;
+        const double* w = seed ? Lj : W + (size_t)i * cap;
+        const double* s1 = seed ? sA : sI;
+        double a[TW] = {}, v[TW] = {};
+        for (int l = lane; l < cl; l += 32) {
+            const double wl = w[l];
+            const double2 p0 = *reinterpret_cast<const double2*>(s1 + l * TW);
+            const double2 p1 = *reinterpret_cast<const double2*>(s1 + l * TW + 2);
+            a[0] = fma(wl, p0.x, a[0]);
+            a[1] = fma(wl, p0.y, a[1]);
+            a[2] = fma(wl, p1.x, a[2]);
+            a[3] = fma(wl, p1.y, a[3]);
+            if (!seed) {
+                const double2 q0 = *reinterpret_cast<const double2*>(sB + l * TW);
+                const double2 q1 = *reinterpret_cast<const double2*>(sB + l * TW + 2);
+                v[0] = fma(wl, q0.x, v[0]);
+                v[1] = fma(wl, q0.y, v[1]);
+                v[2] = fma(wl, q1.x, v[2]);
+                v[3] = fma(wl, q1.y, v[3]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < TW; ++c)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                a[c] += __shfl_xor_sync(0xffffffffu, a[c], o);
+                v[c] += __shfl_xor_sync(0xffffffffu, v[c], o);
+            }
+        if (lane == 0) {
+            double dot = 0.0;
+#pragma unroll
+            for (int c = 0; c < TW; ++c)
+                if (r0 + c < cr) {
+                    Wn[(size_t)i * cap + r0 + c] = a[c];
+                    dot = fma(v[c], Rn[r0 + c], dot);
+                }
+            if (!seed) part[(((size_t)b * n + j) * ntiles + tile) * n + i] = dot;
+        }
+    }
+}
+
+// full[b][i][j] = sum over the tiles of step j of part[b][j][tile][i], / E0
+__global__ void two_reduce_kernel(const double* part, const int* dims, const double* envL,
+                                  const unsigned char* need, int n, int cap, int B, int ntiles, double* full) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)B * n * n) return;
+    const int b = (int)(t / ((long long)n * n)), i = (int)((t / n) % n), j = (int)(t % n);
+    if (j <= i || !need[i]) return;
+    const int cr = dims[(size_t)b * (n + 1) + j + 1];
+    const int nt = (cr + TW - 1) / TW;
+    double sum = 0.0;
+    for (int k = 0; k < nt; ++k) sum += part[(((size_t)b * n + j) * ntiles + k) * n + i];
+    full[((size_t)b * n + i) * n + j] = sum / envL[((size_t)b * (n + 1) + n) * cap];
 }
 
 // trip[t] = (i, j, k): out[b][k] = full[b][i][j] (minus one_a[b][i] one_b[b][j] if connected)
@@ -208,8 +281,13 @@ cudaError_t launch_trace_normalize(void* sites, int sites_f32, const int* dims, 
 
 cudaError_t launch_environments(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                                 double* envL, double* envR, cudaStream_t st) {
-    env_kernel<<<dim3(B, 2), MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR);
-    return cudaGetLastError();
+    const dim3 grid((chi_cap + EW - 1) / EW, 2, B);
+    for (int t = 0; t < n; ++t) {
+        env_step_kernel<<<grid, 256, 0, st>>>(sites, sites_f32, dims, n, chi_cap, t, envL, envR);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_measure_1q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
@@ -220,10 +298,25 @@ cudaError_t launch_measure_1q(const void* sites, int sites_f32, const int* dims,
     return cudaGetLastError();
 }
 
+size_t two_stack_doubles(int n, int B, int chi_cap) { return (size_t)2 * B * n * chi_cap; }
+size_t two_part_doubles(int n, int B, int chi_cap) { return (size_t)B * n * n * ((chi_cap + TW - 1) / TW); }
+
 cudaError_t launch_measure_2q(const void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                               const double* envL, const double* envR, int ca, int cb, const unsigned char* d_need_i,
-                              double* full, cudaStream_t st) {
-    two_kernel<<<dim3(n, B), MT, 0, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR, ca, cb, d_need_i, full);
+                              double* wstack, double* part, double* full, cudaStream_t st) {
+    const int ntiles = (chi_cap + TW - 1) / TW;
+    const size_t smem = (size_t)3 * chi_cap * TW * sizeof(double);
+    static_assert((size_t)3 * kMaxChi * TW * sizeof(double) <= 48 * 1024, "within the default shared memory");
+    double* w[2] = {wstack, wstack + (size_t)B * n * chi_cap};
+    for (int j = 0; j < n; ++j) {
+        two_stack_kernel<<<dim3(ntiles, B), 256, smem, st>>>(sites, sites_f32, dims, n, chi_cap, envL, envR, ca, cb,
+                                                            d_need_i, j, w[j & 1], w[(j + 1) & 1], part, ntiles);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const long long tot = (long long)B * n * n;
+    two_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(part, dims, envL, d_need_i, n, chi_cap, B,
+                                                                      ntiles, full);
     return cudaGetLastError();
 }
 

@@ -8,13 +8,13 @@
 // of matrix multiplication and its applications", Numer. Algorithms 59, 2012):
 //
 // 1. Slicing (oz_slice_kernel).  Each row i of A is scaled by 2^-e_i, e_i the
-//    binary exponent of its largest |A_ik| (so |a| < 1), and cut into S = 6
-//    slices a = 2^-7 sum_t sigma_t 2^-8t with integers |sigma_t| <= 128
-//    (sigma_0 = rint(128 a), each later slice the rint of 256 x the
-//    remainder); a slice keeps 8 significant bits, so it is exact in bf16
-//    (MPDO_MIXED_BF16X3) and in tf32 (MPDO_MIXED_TF32), and it is stored as
-//    sigma_t 2^-8t.  B is cut the same way per column j (exponent f_j).  The
-//    remainder after six slices is below 2^-48 of the row's largest entry.
+//    binary exponent of its largest |A_ik| (so |a| < 1), rounded to the
+//    integer X = round(2^47 a) and cut into S = 6 balanced base-256 digits,
+//    a ~ 2^-7 sum_t sigma_t 2^-8t with integers |sigma_t| <= 128; a slice
+//    keeps 8 significant bits, so it is exact in bf16 (MPDO_MIXED_BF16X3) and
+//    in tf32 (MPDO_MIXED_TF32), and it is stored as sigma_t 2^-8t.  B is cut
+//    the same way per column j (exponent f_j).  The rounding error is at most
+//    2^-48 of the row's largest entry.
 // 2. Products (oz_gemm_kernel).  Every slice pair (t, u) with t + u <= 5 is
 //    multiplied on the tensor core: a product sigma_t sigma_u has at most 16
 //    bits, so it is exact in FP32, and the sums stay exact while they fit 24
@@ -24,7 +24,8 @@
 //    products of up to 2^14 fit 2^22, so levels 0 to 3 (at most four pairs,
 //    2^24) are summed without any rounding, whatever rounding and alignment
 //    the tensor core's FP32 accumulation uses; levels 4 and 5 round at 2^-24
-//    of themselves, below 2^-50 of the result.  (Folding levels 3-5 into one
+//    of themselves, below 2^-50 of the result.  A drain joins the six levels
+//    into one int64 (their exact integer parts) and adds it in FP64.  (Folding levels 3-5 into one
 //    accumulator was measured at 2e-12 on the GPU: the accumulator then holds
 //    level-3 magnitudes and drops the low bits of every level-5 product at
 //    every MMA.)
@@ -165,32 +166,113 @@ __device__ __forceinline__ int pair_u(int p) {
     return U[p];
 }
 
-// element r, k of an operand view (double)
-__device__ __forceinline__ double oz_load(const OzOperand& X, int r, int k) {
-    size_t i;
-    if (X.mode == 1)
-        i = ((size_t)k * 4 + (size_t)(r / X.cr)) * X.cap + (r % X.cr);
-    else
-        i = (size_t)(X.gather ? X.gather[r] : r) * X.rs + (size_t)k * X.ks;
-    return X.f32 ? (double)static_cast<const float*>(X.base)[i] : static_cast<const double*>(X.base)[i];
+// index of element (r, k) of an operand view
+__device__ __forceinline__ size_t oz_index(const OzOperand& X, int r, int k) {
+    if (X.mode == 1) return ((size_t)k * 4 + (size_t)(r / X.cr)) * X.cap + (r % X.cr);
+    return (size_t)(X.gather ? X.gather[r] : r) * X.rs + (size_t)k * X.ks;
 }
 
-// The slices of G consecutive values x[0..G) of one row (exponent e), stored
-// as 16 bytes per slice.
+// The slicing works on bit patterns with integer arithmetic only: GB300
+// issues FP64 instructions at a small fraction of its integer and FP32 rate,
+// and the FP64 form of the same cut (scale, round, subtract, repeat) costs
+// about 25 of them per element.
+//
+// Bit pattern of element (r, k), zero-extended (f32 views: 32 bits).
+__device__ __forceinline__ unsigned long long oz_bits(const OzOperand& X, int r, int k) {
+    const size_t i = oz_index(X, r, k);
+    return X.f32 ? (unsigned long long)__float_as_uint(static_cast<const float*>(X.base)[i])
+                 : (unsigned long long)__double_as_longlong(static_cast<const double*>(X.base)[i]);
+}
+
+// |x| as an unsigned key that orders like |x| within one storage type
+__device__ __forceinline__ unsigned long long abs_key(unsigned long long bits, bool f32) {
+    return f32 ? (bits & 0x7fffffffull) : (bits & 0x7fffffffffffffffull);
+}
+
+__device__ __forceinline__ bool key_nonfinite(unsigned long long key, bool f32) {
+    return f32 ? key >= 0x7f800000ull : key >= 0x7ff0000000000000ull;
+}
+
+// e with 2^(e-1) <= max |x| < 2^e from the largest key (0 for a zero row)
+__device__ __forceinline__ int key_exponent(unsigned long long key, bool f32) {
+    if (key == 0) return 0;
+    int e = 0;
+    if (f32) {
+        const int E = (int)(key >> 23);
+        if (E > 0) return E - 126;
+        frexp((double)__uint_as_float((unsigned)key), &e);      // subnormal float
+    } else {
+        const int E = (int)(key >> 52);
+        if (E > 0) return E - 1022;
+        frexp(__longlong_as_double((long long)key), &e);        // subnormal double
+    }
+    return e;
+}
+
+// X = round(x 2^(47 - e)) for a finite x = +-m 2^p of a row with exponent e
+// (|x| < 2^e, so |X| <= 2^47), ties away from zero
+__device__ __forceinline__ long long fixed_of(unsigned long long bits, bool f32, int e) {
+    bool neg;
+    unsigned long long m;
+    int p;
+    if (f32) {
+        neg = (bits >> 31) & 1;
+        const int E = (int)((bits >> 23) & 0xff);
+        m = bits & 0x7fffffull;
+        if (E) {
+            m |= 1ull << 23;
+            p = E - 150;
+        } else {
+            p = -149;
+        }
+    } else {
+        neg = bits >> 63;
+        const int E = (int)((bits >> 52) & 0x7ff);
+        m = bits & 0xfffffffffffffull;
+        if (E) {
+            m |= 1ull << 52;
+            p = E - 1075;
+        } else {
+            p = -1074;
+        }
+    }
+    const int sh = p + 47 - e;
+    long long X;
+    if (m == 0)
+        X = 0;
+    else if (sh >= 0)
+        X = (long long)(m << (sh < 63 ? sh : 63));   // m 2^sh < 2^47: no bits leave
+    else if (sh <= -62)
+        X = 0;
+    else
+        X = (long long)((m + (1ull << (-sh - 1))) >> -sh);
+    return neg ? -X : X;
+}
+
+// The slices of G consecutive fixed-point values X[0..G) (|X| <= 2^47):
+// balanced base-256 digits X = sum_t sigma_t 2^(8(5 - t)), |sigma_t| <= 128,
+// from the lowest digit up; stored as sigma_t 2^-8t, 16 bytes per slice.
+// nan: the row has a non-finite entry, every slice is NaN.
 template <int G, bool kBf16>
-__device__ __forceinline__ void slice_group(const double* x, int e, uint4* out /* [kS] */) {
-    double rem[G];
+__device__ __forceinline__ void slice_group(const long long* X, bool nan, uint4* out /* [kS] */) {
+    int sig[kS][G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) rem[g] = ldexp(x[g], 7 - e);   // |rem| < 128
+    for (int g = 0; g < G; ++g) {
+        long long d = X[g];
+#pragma unroll
+        for (int t = kS - 1; t > 0; --t) {
+            const int lo = (int)(((unsigned)d + 128u) & 255u) - 128;
+            sig[t][g] = lo;
+            d = (d - lo) >> 8;                                      // exact: d - lo = 0 mod 256
+        }
+        sig[0][g] = (int)d;
+    }
 #pragma unroll
     for (int t = 0; t < kS; ++t) {
+        const float scale = __int_as_float((127 - 8 * t) << 23);   // 2^-8t
         float sl[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-            const double q = rint(rem[g]);
-            rem[g] = (rem[g] - q) * 256.0;                         // exact: |rem - q| <= 1/2
-            sl[g] = (float)ldexp(q, -8 * t);                       // <= 8 significant bits: exact
-        }
+        for (int g = 0; g < G; ++g) sl[g] = nan ? __int_as_float(0x7fc00000) : (float)sig[t][g] * scale;
         if constexpr (kBf16) {
             uint32_t w[4];
 #pragma unroll
@@ -215,41 +297,35 @@ __device__ void slice_rows_tiled(const OzOperand& X, int r0, int R, int K, int K
     constexpr int esize = kBf16 ? 2 : 4;
     constexpr int G = 16 / esize;
     constexpr int KT = kt_elems(esize);
-    __shared__ double s_mx[8][32];
-    __shared__ int s_bad[8][32];
+    __shared__ unsigned long long s_mx[8][32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool f32 = X.f32 != 0;
     const int r = r0 + lane;
     const bool live = r < R;
-    double mx = 0.0;
-    int bad = 0;
+    unsigned long long mx = 0;
     if (live)
         for (int k = warp; k < K; k += 8) {
-            const double v = oz_load(X, r, k);
-            mx = fmax(mx, fabs(v));
-            bad |= !isfinite(v);
+            const unsigned long long key = abs_key(oz_bits(X, r, k), f32);
+            mx = key > mx ? key : mx;
         }
     s_mx[warp][lane] = mx;
-    s_bad[warp][lane] = bad;
     __syncthreads();
-    for (int w = 0; w < 8; ++w) {
-        mx = fmax(mx, s_mx[w][lane]);
-        bad |= s_bad[w][lane];
-    }
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);
+    for (int w = 0; w < 8; ++w) mx = s_mx[w][lane] > mx ? s_mx[w][lane] : mx;
+    const bool bad = key_nonfinite(mx, f32);   // the largest key of a row with a NaN or an inf is one
+    const int e = bad ? 0 : key_exponent(mx, f32);
     if (warp == 0) ex[r] = e;
     const int rt = r / tile, rr = r % tile;
     const size_t block = (size_t)tile * 64;
     const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
     for (int g0 = warp * G; g0 < Kt * KT; g0 += 8 * G) {
-        double x[G];
+        long long x[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = g0 + g;
-            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
+            x[g] = (live && !bad && k < K) ? fixed_of(oz_bits(X, r, k), f32, e) : 0;
         }
         uint4 sl[kS];
-        slice_group<G, kBf16>(x, e, sl);
+        slice_group<G, kBf16>(x, bad && live, sl);
         const int kt = g0 / KT, kk = g0 % KT;
 #pragma unroll
         for (int t = 0; t < kS; ++t) {
@@ -287,32 +363,33 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const OzProblem* probs) {
     const int r = blockIdx.x * 8 + warp;
     if (r >= Rt * tile) return;
     const bool live = r < R;
-    double mx = 0.0;
-    bool bad = false;
+    const bool f32 = X.f32 != 0;
+    unsigned long long mx = 0;
     if (live)
         for (int k = lane; k < K; k += 32) {
-            const double v = oz_load(X, r, k);
-            mx = fmax(mx, fabs(v));          // fmax drops NaN: non-finite rows are flagged apart
-            bad |= !isfinite(v);
+            const unsigned long long key = abs_key(oz_bits(X, r, k), f32);
+            mx = key > mx ? key : mx;
         }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    bad = __any_sync(0xffffffffu, bad);
-    int e = 0;
-    if (mx > 0.0 && isfinite(mx)) frexp(mx, &e);   // mx = f 2^e, f in [0.5, 1): |x| 2^-e < 1
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    const bool bad = key_nonfinite(mx, f32);
+    const int e = bad ? 0 : key_exponent(mx, f32);
     if (lane == 0) ex[r] = e;
     const int rt = r / tile, rr = r % tile;
     const size_t block = (size_t)tile * 64;
     const size_t within = (size_t)(rr >> 3) * SBO + (size_t)(rr & 7) * 16;
     for (int g0 = lane * G; g0 < Kt * KT; g0 += 32 * G) {
-        double x[G];
+        long long x[G];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int k = g0 + g;
-            x[g] = (live && k < K) ? (bad ? __longlong_as_double(0x7ff8000000000000ll) : oz_load(X, r, k)) : 0.0;
+            x[g] = (live && !bad && k < K) ? fixed_of(oz_bits(X, r, k), f32, e) : 0;
         }
         uint4 sl[kS];
-        slice_group<G, kBf16>(x, e, sl);
+        slice_group<G, kBf16>(x, bad && live, sl);
         const int kt = g0 / KT, kk = g0 % KT;
 #pragma unroll
         for (int t = 0; t < kS; ++t) {
@@ -456,16 +533,36 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
+            // level d holds n_d 2^-8d with n_d an integer (exact for d <= 3;
+            // levels 4 and 5 are rounded to the nearest 2^-32 and 2^-40):
+            // the range's sum is S 2^-40 with the integer
+            // S = sum_d n_d 2^(8 (5 - d)), |S| < 2^63, formed in int64 and
+            // converted once (integer arithmetic instead of twelve FP64
+            // operations per element).  A NaN slice reaches level 0.
 #pragma unroll
-            for (int lvl = 0; lvl < kLevels; ++lvl) {
+            for (int c = 0; c < 2; ++c) {
+                long long S[16];
+                unsigned nan = 0;
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
+                for (int lvl = 0; lvl < kLevels; ++lvl) {
                     float v[16];
                     tmem_ld16(taddr + (uint32_t)(lvl * kTileN + c * 16), v);
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const float scale = __int_as_float((127 + 8 * lvl) << 23);   // 2^8d
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[c * 16 + i] += (double)v[i];
+                    for (int i = 0; i < 16; ++i) {
+                        const long long n = __float2int_rn(v[i] * scale);
+                        if (lvl == 0) {
+                            S[i] = n;
+                            nan |= (v[i] != v[i]) ? 1u << i : 0u;
+                        } else {
+                            S[i] = S[i] * 256 + n;
+                        }
+                    }
                 }
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    acc[c * 16 + i] += ((nan >> i) & 1u) ? __longlong_as_double(0x7ff8000000000000ll) : (double)S[i];
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -480,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, 1) oz_gemm_kernel(const OzProblem* p
                 for (int jj = 0; jj < 32; ++jj) {
                     const int j = nt * kTileN + half * 32 + jj;
                     if (j >= N) continue;
-                    double v = P.alpha * ldexp(acc[jj], ei + P.eb[j] - 14);
+                    double v = P.alpha * ldexp(acc[jj], ei + P.eb[j] - 54);   // acc in units of 2^-40
                     const size_t row = P.c_gather ? (size_t)P.c_gather[i] : (size_t)i;
                     if (P.D) {
                         const size_t di = row * P.ldd + j;

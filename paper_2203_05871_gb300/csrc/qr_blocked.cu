@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
     extern __shared__ double P[];   // panel, column-major: P[j * mp + i]; then the window's norms
     __shared__ double red[kThreads / 32][kSums];
     __shared__ double s_sum[kSums];
-    __shared__ double s_pn[kMaxNb], s_beta[kMaxNb], s_w[kMaxNb], s_z[kMaxNb];
+    __shared__ double s_pn[kMaxNb], s_w[kMaxNb], s_z[kMaxNb];
     __shared__ double s_best[kThreads / 32];
     __shared__ int s_bidx[kThreads / 32];
     __shared__ int s_piv, s_redo;
@@ -229,7 +229,6 @@ __global__ void __launch_bounds__(kThreads, 1) qrb_panel_kernel(const OpDesc* de
         // reflector j as row j of V (zeros above its pivot row)
         double* vr = s.V + (size_t)j * ld;
         for (int i = tid; i < mp; i += kThreads) vr[i] = i < j ? 0.0 : (i == j ? v0 : x[i]);
-        if (tid == 0) s_beta[j] = beta;
         if (tid > j && tid < jb) s_w[tid] = fma(v0, P[tid * mp + j], s_sum[tid]);   // w_q = v . y_q
         // T column j: z_t = v_t . v_j = v_t[j] v0 + (x . v_t below row j), then
         // T[t][j] = -beta_j sum_{t <= l < j} T[t][l] z_l, T[j][j] = beta_j

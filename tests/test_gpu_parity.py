@@ -157,6 +157,40 @@ def test_decoupled_grid40_chi512():
         assert abs(z[q] - c[3]) < 1e-12
 
 
+def test_observables_snake40_chi512_sampled():
+    """Measurement at full size: the 4x10 snake (N = 40) holding a seeded random
+    MPO at chi 512 (bonds saturated from position 4 inward).  Every <Z_i> and
+    all 780 pairs (both orders, connected) are measured through the stacked
+    all-pairs path; the <Z_i> and a sample of pairs are checked against the
+    oracle's MPO traces.  The values are ratios of traces of a non-physical
+    MPO, so the bound is relative to their size."""
+    wl = W.grid4x10_snake()
+    n = wl.n
+    dims, tens = W.random_mpo_state(n, 512, seed=2203058712 + 3, decay=0.02)
+    s = solver_for(wl, chi_cap=512, max_slots=1)
+    s.set_state(0, dims, tens)
+    st = tebd.MPOState(tens, [np.ones(d) for d in dims[1:-1]])
+    z = s.measure_1q(range(n), "Z")[0]
+    rz = np.array([st.expect_1q(i) for i in range(n)])
+    assert np.all(np.abs(z - rz) <= 1e-10 * np.maximum(1.0, np.abs(rz)))
+    pairs = [(i, j) for i in range(n) for j in range(n) if i != j]
+    g = s.measure_2q(pairs, "ZZ", connected=True)[0]
+    rng = np.random.default_rng(5)
+    sample = sorted(set(rng.choice(len(pairs), 120, replace=False).tolist()) |
+                    {pairs.index(p) for p in [(0, 39), (39, 0), (0, 1), (38, 39), (19, 20), (20, 19)]})
+    for k in sample:
+        i, j = pairs[k]
+        zz = st.expect_2q(min(i, j), max(i, j))
+        ref = zz - rz[i] * rz[j]
+        assert abs(g[k] - ref) <= 1e-10 * max(1.0, abs(zz) + abs(rz[i] * rz[j])), (i, j, g[k], ref)
+    # mixed components: <X_i Z_j> = <Z_j X_i> through both orders of the pair
+    xz = s.measure_2q([(3, 17), (17, 3)], "XZ", connected=False)[0]
+    ref = st.expect_2q(3, 17, ("X", "Z"))
+    assert abs(xz[0] - ref) <= 1e-10 * max(1.0, abs(ref))
+    ref2 = st.expect_2q(3, 17, ("Z", "X"))
+    assert abs(xz[1] - ref2) <= 1e-10 * max(1.0, abs(ref2))
+
+
 def test_single_excitation_ring24_and_grid():
     from tests.test_oracle_pins import single_excitation
     for n, bonds in [(24, W.ring_bonds(24)), (40, W.grid_snake_bonds(10, 4))]:
