@@ -439,7 +439,7 @@ def run_observables(args, local, reps=5):
     n, chi = wl.n, 512
     dims, tens = W.random_mpo_state(n, chi, seed=2203058712 + 3, decay=DECAY)
     stream = torch.cuda.Stream()
-    s = Solver(n, batch=1, chi_cap=chi, stream=stream, precision=FP64, max_slots=1)
+    s = Solver(n, batch=1, chi_cap=chi, stream=stream, precision=FP64, max_slots=2)
     s.build_gates(wl)
     s.set_state(0, dims, tens)
     pairs = [(i, j) for i in range(n) for j in range(i + 1, n)]

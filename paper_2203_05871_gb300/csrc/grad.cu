@@ -91,6 +91,9 @@ struct GradState {
     BwdDesc *h_bd = nullptr, *d_bd = nullptr;
     GemmDesc *h_bg = nullptr, *d_bg = nullptr;   // [kBwdGemms][bslots]
     Copy2D *h_bc = nullptr, *d_bc = nullptr;     // [5][bslots]
+    // mixed path: the backward products on the tensor cores (one slot per op in flight)
+    unsigned char* d_oz = nullptr;
+    OzScratch oz{};
     // adjoint state and loss
     double *d_sbar = nullptr, *d_lbar = nullptr, *d_gacc = nullptr, *d_contrib = nullptr, *d_grad = nullptr;
     double *d_a = nullptr, *d_W = nullptr, *d_ls = nullptr;
@@ -102,7 +105,7 @@ void grad_free(GradState* g) {
     if (!g) return;
     g->ck.reset();
     void* ptrs[] = {g->d_traces, g->d_cp, g->d_tape, g->d_ws,   g->d_bd, g->d_bg, g->d_bc,  g->d_sbar,
-                    g->d_lbar,   g->d_gacc, g->d_contrib, g->d_grad, g->d_a, g->d_W, g->d_ls};
+                    g->d_lbar,   g->d_gacc, g->d_contrib, g->d_grad, g->d_a, g->d_W, g->d_ls, g->d_oz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* hptrs[] = {g->h_cp, g->h_bd, g->h_bg, g->h_bc};
@@ -185,13 +188,15 @@ int alloc_backward(mpdo_ctx* c, GradState* g) {
         g->alloc_P == P)
         return MPDO_OK;
     void* ptrs[] = {g->d_ws, g->d_bd, g->d_bg, g->d_bc, g->d_sbar, g->d_lbar, g->d_gacc, g->d_contrib,
-                    g->d_grad, g->d_a, g->d_W, g->d_ls};
+                    g->d_grad, g->d_a, g->d_W, g->d_ls, g->d_oz};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* hptrs[] = {g->h_bd, g->h_bg, g->h_bc};
     for (void* p : hptrs)
         if (p) cudaFreeHost(p);
     g->d_ws = g->d_sbar = g->d_lbar = g->d_gacc = g->d_contrib = g->d_grad = g->d_a = g->d_W = g->d_ls = nullptr;
+    g->d_oz = nullptr;
+    g->oz = OzScratch{};
     g->d_bd = g->h_bd = nullptr;
     g->d_bg = g->h_bg = nullptr;
     g->d_bc = g->h_bc = nullptr;
@@ -217,12 +222,31 @@ int alloc_backward(mpdo_ctx* c, GradState* g) {
     g->ls.coef = q;
     // backward slots: as many ops in flight as a layer has, within half the free memory
     g->ws_slot = (size_t)12 * ld * cap + (size_t)2 * ld * ld + (size_t)kGateBwdParts * 256;
+    // mixed path: slices of both operands of one product per slot, every dimension <= ld
+    const size_t oz_bytes = (size_t)256 * ((oz_slice_bytes(ld, ld, c->oz_bf16) + 255) / 256);
+    const size_t oz_ints = oz_exp_ints(ld);
+    const size_t oz_slot = c->mixed ? 2 * oz_bytes + 2 * oz_ints * sizeof(int) + sizeof(OzProblem) : 0;
     size_t free_b = 0, total_b = 0;
     CU(cudaMemGetInfo(&free_b, &total_b));
     const int want = B * c->max_layer;
-    int s = (int)std::max<size_t>(1, std::min<size_t>(want, free_b / 2 / (g->ws_slot * sizeof(double))));
+    int s = (int)std::max<size_t>(
+        1, std::min<size_t>(want, free_b / 2 / (g->ws_slot * sizeof(double) + oz_slot)));
     if (c->cfg.max_slots > 0) s = std::min(s, c->cfg.max_slots);
     CU(dalloc(&g->d_ws, (size_t)s * g->ws_slot));
+    if (c->mixed) {
+        CU(dalloc(&g->d_oz, (size_t)s * oz_slot));
+        unsigned char* q8 = g->d_oz;
+        g->oz.as = q8;
+        q8 += (size_t)s * oz_bytes;
+        g->oz.bs = q8;
+        q8 += (size_t)s * oz_bytes;
+        g->oz.probs = reinterpret_cast<OzProblem*>(q8);   // 256-byte aligned: oz_bytes is a multiple
+        q8 += (size_t)s * sizeof(OzProblem);
+        g->oz.ea = reinterpret_cast<int*>(q8);
+        g->oz.eb = g->oz.ea + (size_t)s * oz_ints;
+        g->oz.slot_bytes = oz_bytes;
+        g->oz.exp_ints = oz_ints;
+    }
     CU(dalloc(&g->d_bd, (size_t)s));
     CU(dalloc(&g->d_bg, (size_t)kBwdGemms * s));
     CU(dalloc(&g->d_bc, (size_t)5 * s));
@@ -250,7 +274,7 @@ int run_bwd_chunk(mpdo_ctx* c, GradState* g, const std::vector<const TapeRec*>& 
     BwdDesc* bd = g->h_bd;
     GemmDesc* bg = g->h_bg;
     Copy2D* bc = g->h_bc;
-    int mx[kBwdGemms][2] = {};
+    int mx[kBwdGemms][3] = {};
     int max_pack = 1, max_unpack = 1, max_cl = 1;
     for (int s = 0; s < nops; ++s) {
         const TapeRec& t = *recs[s];
@@ -321,15 +345,24 @@ int run_bwd_chunk(mpdo_ctx* c, GradState* g, const std::vector<const TapeRec*>& 
             gd(cm, n, m, Ac, cm, 1, X2, n, 0, Vb, n),                      // 9: B-bar = A^T Theta-bar
         };
         for (int q = 0; q < kBwdGemms; ++q) {
+            gl[q].status = c->d_status + t.b;
             bg[(size_t)q * S + s] = gl[q];
             mx[q][0] = std::max(mx[q][0], gl[q].M);
             mx[q][1] = std::max(mx[q][1], gl[q].N);
+            mx[q][2] = std::max(mx[q][2], gl[q].K);
         }
     }
     CU(cudaMemcpyAsync(g->d_bd, bd, sizeof(BwdDesc) * nops, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(g->d_bg, bg, sizeof(GemmDesc) * kBwdGemms * S, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(g->d_bc, bc, sizeof(Copy2D) * 5 * nops, cudaMemcpyHostToDevice, c->st));
-    auto gemm = [&](int q) { return launch_gemm(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], false, c->st); };
+    // the mixed path runs the products on the tensor cores (FP64-accurate slice
+    // products, oz_gemm.cu), the FP64 path on the FP64 pipe (gemm.cu)
+    const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
+    auto gemm = [&](int q) {
+        return c->mixed ? launch_gemm_tc(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], mx[q][2], g->oz,
+                                         c->oz_bf16, timeout_ns, c->st)
+                        : launch_gemm(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], false, c->st);
+    };
     CU(launch_copy2d(g->d_bc, 2 * nops, max_pack, c->st));
     CU(gemm(0));
     CU(gemm(1));

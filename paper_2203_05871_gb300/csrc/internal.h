@@ -253,9 +253,22 @@ struct GemmDesc {
     int a_trans;      // A stored K x M (default 0)
     int sym;          // 1: C is symmetric (A B with B = A^T, D = nullptr): only the tiles on and
                       // above the diagonal are computed, each written to both triangles
+    int* status;      // tensor-core route: MPDO_ST_TIMEOUT lands here (or nullptr)
 };
 cudaError_t launch_gemm(const GemmDesc* d_desc, int count, int max_m, int max_n, bool fp32_compute,
                         cudaStream_t st);
+// The batched GemmDesc products (f64 operands, sym computed in full) on the
+// tensor cores: problem s takes slot s of the scratch (slices of slot_bytes per
+// operand, exponents of exp_ints per operand, oz_slice_bytes / oz_exp_ints of
+// the largest dimension) and probs[s]; max_m, max_n, max_k bound every product.
+struct OzScratch {
+    unsigned char *as, *bs;
+    int *ea, *eb;
+    OzProblem* probs;
+    size_t slot_bytes, exp_ints;
+};
+cudaError_t launch_gemm_tc(const GemmDesc* d_desc, int count, int max_m, int max_n, int max_k, const OzScratch& scr,
+                           bool bf16, unsigned long long timeout_ns, cudaStream_t st);
 
 cudaError_t launch_trace_normalize(void* sites, int sites_f32, const int* dims, int n, int B, int chi_cap,
                                    int force, double* trace_out, int* status, cudaStream_t st);

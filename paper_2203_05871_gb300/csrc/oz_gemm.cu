@@ -760,6 +760,55 @@ cudaError_t launch_oz_gemm(const OzProblem* d_probs, int count, int max_m, int m
     return cudaGetLastError();
 }
 
+namespace {
+
+// problem s of a GemmDesc batch as an OzProblem (one thread per problem)
+__global__ void gemm_desc_oz_kernel(const GemmDesc* descs, int count, OzScratch scr, int bf16) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= count) return;
+    const GemmDesc& d = descs[s];
+    OzProblem P{};
+    P.M = d.M;
+    P.N = d.N;
+    P.K = d.K;
+    // A (M x K): stored M x K, or K x M when a_trans
+    P.A = d.a_trans ? OzOperand{d.A, d.a_f32, 1, d.lda, 0, 1, 1, nullptr}
+                    : OzOperand{d.A, d.a_f32, d.lda, 1, 0, 1, 1, nullptr};
+    // column j of B (K x N) as a row of K values: stored K x N, or N x K when b_trans
+    P.B = d.b_trans ? OzOperand{d.B, d.b_f32, d.ldb, 1, 0, 1, 1, nullptr}
+                    : OzOperand{d.B, d.b_f32, 1, d.ldb, 0, 1, 1, nullptr};
+    P.C = d.C;
+    P.ldc = d.ldc;
+    P.alpha = d.alpha;
+    P.beta = d.beta;
+    P.D = d.D;
+    P.ldd = d.ldd;
+    P.d_f32 = d.d_f32;
+    P.sub_identity = d.sub_identity;
+    P.as = scr.as + (size_t)s * scr.slot_bytes;
+    P.bs = scr.bs + (size_t)s * scr.slot_bytes;
+    P.ea = scr.ea + (size_t)s * scr.exp_ints;
+    P.eb = scr.eb + (size_t)s * scr.exp_ints;
+    P.status = d.status;
+    oz_set_tiles(P, bf16 != 0);
+    scr.probs[s] = P;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(const GemmDesc* d_desc, int count, int max_m, int max_n, int max_k, const OzScratch& scr,
+                           bool bf16, unsigned long long timeout_ns, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    // every operand must fit its slot
+    const int big = max_m > max_n ? max_m : max_n;
+    if (oz_slice_bytes(big, max_k, bf16) > scr.slot_bytes || oz_exp_ints(big) > scr.exp_ints)
+        return cudaErrorInvalidValue;
+    gemm_desc_oz_kernel<<<(count + 127) / 128, 128, 0, st>>>(d_desc, count, scr, bf16 ? 1 : 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_oz_gemm(scr.probs, count, max_m, max_n, big, bf16, timeout_ns, st);
+}
+
 }  // namespace mpdo
 
 // ---------------------------------------------------------------------------
