@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="skip the graph-replayed steps")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the observables timing on the 4x10 snake at chi 512")
+    ap.add_argument("--precond-rho", type=float, default=0.0,
+                    help="mixed path: largest FP32 rotation at which the preconditioning sweeps stop (0: default)")
     ap.add_argument("--qr-blocked", action="store_true",
                     help="mixed path: blocked Householder QR (tensor-core trailing updates) instead of the column QR")
     ap.add_argument("--adjoint-steps", type=int, default=1,
@@ -312,7 +314,7 @@ def run_arm(args, precision, world, dist, local, workload=None, steps=None, warm
     mixed = MIXED_BF16X3 if args.mixed_kind == "bf16" else MIXED_TF32
     s = Solver(wl.n, batch=wl.batch, chi_cap=cap, stream=stream,
                precision=FP64 if precision == "fp64" else mixed, max_slots=max_slots,
-               qr_blocked=args.qr_blocked)
+               qr_blocked=args.qr_blocked, precond_rho=args.precond_rho)
     s.build_gates(wl)
     tuned = None
     if autotune and not args.no_autotune:

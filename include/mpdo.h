@@ -84,6 +84,11 @@ typedef struct {
     int qr_blocked;          /* mixed path only: 1 = blocked Householder QR (window-pivoted panels of
                                 16 columns, trailing updates on the tensor cores); 0 (default) =
                                 the column-by-column QR, measured faster on this GPU */
+    double precond_rho;      /* mixed path only: the FP32 preconditioning sweeps stop after a sweep
+                                whose largest rotation (relative off-orthogonality |g|/sqrt(a b) of
+                                a rotated pair) was at most this (<= 0: 1e-3); a smaller value
+                                trades FP32 sweeps for fewer FP64 finishing sweeps.  Accuracy is
+                                unchanged: the FP64 sweeps finish to the FP64 tolerance. */
 } mpdo_config;
 
 typedef struct {

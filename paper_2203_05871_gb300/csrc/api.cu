@@ -126,7 +126,7 @@ int alloc_slots(mpdo_ctx* c, int want) {
     CU(dalloc(&c->d_desc, (size_t)s));
     const int gcap = std::max(std::max(c->jacobi_resident, c->qr_resident), s);
     CU(dalloc(&c->d_cta, (size_t)3 * (2 * gcap + s)));
-    CU(dalloc(&c->d_sync, (size_t)s * jacobi_sync_words_per_op()));
+    CU(dalloc(&c->d_sync, jacobi_sync_words(s)));
     CU(cudaMallocHost((void**)&c->h_desc, sizeof(OpDesc) * s));
     CU(cudaMallocHost((void**)&c->h_cta, sizeof(int) * 3 * (2 * gcap + s)));
     CU(dalloc(&c->d_copy, (size_t)4 * s));
@@ -363,10 +363,10 @@ int run_chunk(mpdo_ctx* c, const std::vector<Item>& items, int step, const int* 
         int rc = plan(fp32, hbase, total);
         if (rc) return rc;
         CU(cudaMemcpyAsync(dbase, hbase, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
-        CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+        CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words(nops), c->st));
         CU(launch_jacobi(c->d_desc, nops, dbase, dbase + total, dbase + 2 * total, c->d_sync, total,
                          fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : fp64_jacobi_tol(c),
-                         timeout_ns, ld, fp32, c->st));
+                         timeout_ns, ld, fp32, c->st, precond_rho(c)));
         return MPDO_OK;
     };
     CU(cudaMemsetAsync(c->d_sweeps, 0, sizeof(int) * nops, c->st));
@@ -602,6 +602,7 @@ int mpdo_init(mpdo_ctx** out, const mpdo_config* cfg, void* cuda_stream) {
     *out = nullptr;
     if (cfg->n_qubits < 3) return fail(MPDO_EINVAL, "n_qubits must be >= 3");
     if (cfg->batch < 1) return fail(MPDO_EINVAL, "batch must be >= 1");
+    if (!(cfg->precond_rho <= 1.0)) return fail(MPDO_EINVAL, "precond_rho must be a number <= 1");
     if (cfg->chi_cap < 1 || cfg->chi_cap > kMaxChi) return fail(MPDO_EINVAL, "chi_cap must be in [1, 512]");
     if (cfg->precision != MPDO_FP64 && cfg->precision != MPDO_MIXED_TF32 && cfg->precision != MPDO_MIXED_BF16X3)
         return fail(MPDO_EINVAL, "precision must be MPDO_FP64, MPDO_MIXED_TF32 or MPDO_MIXED_BF16X3");

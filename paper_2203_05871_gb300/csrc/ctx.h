@@ -204,6 +204,9 @@ void fill_desc(mpdo_ctx* c, const Item& it, int s, OpDesc& d);
 // five orders inside the mixed path's 1e-5 bound) instead of sqrt(L) eps;
 // the FP64 path, an explicit jacobi_tol and the gradient keep the strict one.
 constexpr double kMixedFinishTol = 1e-10;
+// largest rotation (relative off-orthogonality) of the FP32 preconditioning
+// sweep after which that pass stops
+inline double precond_rho(const mpdo_ctx* c) { return c->cfg.precond_rho > 0.0 ? c->cfg.precond_rho : 1e-3; }
 inline double fp64_jacobi_tol(const mpdo_ctx* c) {
     return (c->cfg.jacobi_tol <= 0.0 && c->mixed && !c->full_svd) ? kMixedFinishTol : c->cfg.jacobi_tol;
 }

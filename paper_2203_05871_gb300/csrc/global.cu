@@ -251,7 +251,7 @@ int run_svd(mpdo_ctx* c, double* W, const std::vector<int>& slots, const std::ve
     int rc = plan_jacobi(c, c->h_desc, nops, false, c->h_cta, total);
     if (rc) return rc;
     CU(cudaMemcpyAsync(c->d_cta, c->h_cta, sizeof(int) * (2 * total + nops), cudaMemcpyHostToDevice, c->st));
-    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words(nops), c->st));
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
     CU(launch_jacobi(c->d_desc, nops, c->d_cta, c->d_cta + total, c->d_cta + 2 * total, c->d_sync, total,
                      c->cfg.jacobi_max_sweeps, 0.0, timeout_ns, ld, false, c->st));

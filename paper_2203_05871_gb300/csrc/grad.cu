@@ -355,13 +355,23 @@ int run_bwd_chunk(mpdo_ctx* c, GradState* g, const std::vector<const TapeRec*>& 
     CU(cudaMemcpyAsync(g->d_bd, bd, sizeof(BwdDesc) * nops, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(g->d_bg, bg, sizeof(GemmDesc) * kBwdGemms * S, cudaMemcpyHostToDevice, c->st));
     CU(cudaMemcpyAsync(g->d_bc, bc, sizeof(Copy2D) * 5 * nops, cudaMemcpyHostToDevice, c->st));
-    // the mixed path runs the products on the tensor cores (FP64-accurate slice
-    // products, oz_gemm.cu), the FP64 path on the FP64 pipe (gemm.cu)
+    // The mixed path runs products 4, 6, 7, 8 and 9 on the tensor cores (slice
+    // products, oz_gemm.cu), the others on the FP64 pipe (gemm.cu).  The slice
+    // products bound their error by 2^-46 of the largest entry of a row of A
+    // times the largest of a column of B, where FP64 bounds each term by its
+    // own size; that is as good wherever the terms of a sum have comparable
+    // sizes.  Products 0-3 feed S_k^-2 (V-bar - V_c K^T), a difference of
+    // nearly equal parts scaled by up to (s_0 / s_k)^2, and product 5 sums
+    // along K the rows of H_k (scale ~ s^-2) with those of V_k (scale 1), so
+    // that V_k's share sits below the slices' resolution: with them on the
+    // tensor cores a directional derivative of the N = 24 ring moved by 1e-3
+    // of itself.
     const unsigned long long timeout_ns = (unsigned long long)c->cfg.barrier_timeout_ms * 1000000ull;
     auto gemm = [&](int q) {
-        return c->mixed ? launch_gemm_tc(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], mx[q][2], g->oz,
-                                         c->oz_bf16, timeout_ns, c->st)
-                        : launch_gemm(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], false, c->st);
+        const bool tc = c->mixed && (q == 4 || q >= 6);
+        return tc ? launch_gemm_tc(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], mx[q][2], g->oz, c->oz_bf16,
+                                   timeout_ns, c->st)
+                  : launch_gemm(g->d_bg + (size_t)q * S, nops, mx[q][0], mx[q][1], false, c->st);
     };
     CU(launch_copy2d(g->d_bc, 2 * nops, max_pack, c->st));
     CU(gemm(0));

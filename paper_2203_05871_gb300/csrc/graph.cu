@@ -178,7 +178,7 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
             } else {
                 CU(launch_merge_gate(ch.d_desc, nops, cap, st));
             }
-            const size_t sync_bytes = sizeof(unsigned) * jacobi_sync_words_per_op() * nops;
+            const size_t sync_bytes = sizeof(unsigned) * jacobi_sync_words(nops);
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
             if (c->mixed && c->cfg.qr_blocked && qrb_fits(cap))
                 CU(launch_qr_blocked(ch.d_desc, nops, cap, c->d_oz, c->oz_bf16, timeout_ns, st, 0));
@@ -188,14 +188,14 @@ int enqueue_step(mpdo_ctx* c, GraphState* g, cudaStream_t st) {
             if (c->mixed) {
                 CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
                 CU(launch_jacobi(ch.d_desc, nops, ch.d_cta32, ch.d_cta32 + g->Rj, ch.d_cta32 + 2 * g->Rj, c->d_sync,
-                                 g->Rj, kMaxSweepsCap / 2, 0.0, timeout_ns, ld, true, st));
+                                 g->Rj, kMaxSweepsCap / 2, 0.0, timeout_ns, ld, true, st, precond_rho(c)));
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_E, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_Q, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_W, c->d_oz, cap, c->oz_bf16, timeout_ns, st));
             }
             CU(cudaMemsetAsync(c->d_sync, 0, sync_bytes, st));
             CU(launch_jacobi(ch.d_desc, nops, ch.d_cta64, ch.d_cta64 + g->Rj, ch.d_cta64 + 2 * g->Rj, c->d_sync, g->Rj,
-                             c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st));
+                             c->cfg.jacobi_max_sweeps, fp64_jacobi_tol(c), timeout_ns, ld, false, st, precond_rho(c)));
             CU(launch_truncate(ch.d_desc, nops, cap, st));
             if (c->mixed)
                 CU(launch_oz_ops(ch.d_desc, nops, OZ_RECON, c->d_oz, cap, c->oz_bf16, timeout_ns, st));

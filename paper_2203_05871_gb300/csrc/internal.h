@@ -126,19 +126,21 @@ __host__ __device__ inline int jacobi_block_rows(int rowlen, int c, int elem_byt
 }
 // FP32 preconditioning pass: rows of at most kJacobiRegL elements take the
 // register path (one block of b <= kJacobiMaxB rows in shared memory, the
-// other in registers, the U32 part turned afterwards by the block pair's
-// accumulated rotation); longer rows the shared-memory path above.
+// other in registers), longer rows the shared-memory path above; in both the
+// U32 rows are turned once per block pair by its accumulated rotation, so only
+// the L-long W rows are staged.
 constexpr int kJacobiRegL = 1024;
 __host__ __device__ inline bool jacobi_f32_reg(int L) { return L <= kJacobiRegL; }
 __host__ __device__ inline int jacobi_block_rows_f32(int L, int c) {
-    if (!jacobi_f32_reg(L)) return jacobi_block_rows(L + c, c, 4);
+    if (!jacobi_f32_reg(L)) return jacobi_block_rows(L, c, 4);
     int b = kJacobiMaxB;
     while (b > 1 && b >= c) b >>= 1;
     return b;
 }
-// whether b rows per block fit the FP32 pass for rows of length L (plus the c-long U32 part)
+// whether b rows per block fit the FP32 pass for rows of length L
 __host__ __device__ inline bool jacobi_f32_fits(int b, int L, int c) {
-    return jacobi_f32_reg(L) ? b <= kJacobiMaxB : (size_t)2 * b * (L + c) * 4 <= (size_t)kJacobiRowBytes;
+    (void)c;
+    return jacobi_f32_reg(L) ? b <= kJacobiMaxB : (size_t)2 * b * L * 4 <= (size_t)kJacobiRowBytes;
 }
 // block pairs per tournament round
 __host__ __device__ inline int jacobi_pairs_per_round(int c, int b) {
@@ -153,8 +155,11 @@ cudaError_t jacobi_max_resident(int* blocks);
 // W32 is filled from W0, scaled); false: the FP64 pass on (W | Z).
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st);
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st,
+                          double pre_rho = 1e-3);   // FP32 pass: stop once no rotation exceeds pre_rho
 size_t jacobi_sync_words_per_op();
+// sync words of a Jacobi launch over nops ops (theirs and the grid barrier's)
+size_t jacobi_sync_words(int nops);
 
 cudaError_t launch_truncate(const OpDesc* d_desc, int nops, int chi_cap, cudaStream_t st);
 

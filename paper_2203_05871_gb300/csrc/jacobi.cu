@@ -90,8 +90,11 @@ __device__ __forceinline__ T row_dot(const T* x, const T* y, int L, int lane) {
     return warp_sum((s0 + s1) + (s2 + s3));
 }
 
+constexpr int kMS = 2 * kMaxB;   // side of a block pair's accumulated rotation (FP32 pass)
+
 template <typename T>
 struct Ctx {
+    float* M;         // FP32 shared-memory path: the block pair's accumulated rotation [kMS][kMS], else nullptr
     T* rows;          // [2b][rowlen] in shared memory
     T* nrm;           // [2b]
     double* dsc;      // [2b] FP64 pass: the row is dsc times the stored row (scaled rotations)
@@ -251,6 +254,17 @@ __device__ int pair_rotate(const Ctx<T>& C, int p, int q, int lane) {
         rp[i] = fma(cs, x, -sn * y);
         rq[i] = fma(sn, x, cs * y);
     }
+    if constexpr (sizeof(T) == 4) {
+        if (C.M) {   // the same rotation of rows p, q of the accumulator
+            float* mp = C.M + p * kMS;
+            float* mq = C.M + q * kMS;
+            for (int j = lane; j < kMS; j += 32) {
+                const float x = mp[j], y = mq[j];
+                mp[j] = fmaf(cs, x, -sn * y);
+                mq[j] = fmaf(sn, x, cs * y);
+            }
+        }
+    }
     __syncwarp();
     T na = fma(-t, g, a), nb = fma(t, g, b);
     if (na < T(0.1) * a) na = row_dot(rp, rp, C.L, lane);
@@ -315,7 +329,8 @@ constexpr int kRegRows = (kMaxB + RW - 1) / RW;   // block-0 rows per warp at mo
 constexpr int kM = 2 * kMaxB;             // accumulator dimension
 constexpr int kZT = 128;                  // U32 columns per tile of the accumulator product
 constexpr int kSmemReg = kJacobiRegL * kMaxB * 4 + kM * kM * 4 + kM * 12;
-constexpr int kSmemF32 = kSmemReg > kSmemBytes ? kSmemReg : kSmemBytes;
+constexpr int kSmemSmemF32 = kSmemBytes + kM * kM * 4;   // shared-memory path: rows, norms, ids, M
+constexpr int kSmemF32 = kSmemReg > kSmemSmemF32 ? kSmemReg : kSmemSmemF32;
 static_assert(kRegRows * RW >= kMaxB, "block 0 must fit the warps' registers");
 static_assert(RT == (kM / 4) * (kZT / 4), "one 4 x 4 output tile per thread");
 static_assert(kM * kZT + kM * kM <= kJacobiRegL * kMaxB, "U32 tile and M^T fit the rows' space");
@@ -350,6 +365,54 @@ __device__ __forceinline__ void rotate_m(const RegCtx& C, int ip, int iq, float 
         const float x = mp[j], y = mq[j];
         mp[j] = fmaf(cs, x, -sn * y);
         mq[j] = fmaf(sn, x, cs * y);
+    }
+}
+
+// U32 rows <- M U32 rows for the 2b rows of a block pair (rid: their global
+// rows, -1 for none), in column tiles of kZT staged in shared memory at stage
+// (>= kM kZT + kM kM floats, free: the W rows are stored by then): thread
+// (rg, cg) of 16 x 32 computes rows 4 rg .. 4 rg + 3 and columns 4 cg ..
+// 4 cg + 3 of the tile, reading M^T and the tile as float4.  Called by all
+// threads of the CTA.
+__device__ void apply_m_u32(const float* M, const int* rid, int n2, float* Z, int ld, int c, float* stage) {
+    float* Zt = stage;              // [kM][kZT]
+    float* Mt = stage + kM * kZT;   // [kM][kM]: M transposed
+    for (int i = threadIdx.x; i < kM * kM; i += RT) Mt[(i % kM) * kM + i / kM] = M[i];
+    const int rg = threadIdx.x >> 5, cg = threadIdx.x & 31;
+    for (int k0 = 0; k0 < c; k0 += kZT) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kM * (kZT / 4); e += RT) {
+            const int j = e / (kZT / 4), kk = 4 * (e % (kZT / 4));
+            const int row = j < n2 ? rid[j] : -1;
+            float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (row >= 0 && k0 + kk < c) v = __ldcg(reinterpret_cast<const float4*>(Z + (size_t)row * ld + k0 + kk));
+            *reinterpret_cast<float4*>(Zt + j * kZT + kk) = v;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = 0.0f;
+#pragma unroll 4
+        for (int j = 0; j < n2; ++j) {
+            const float4 m = *reinterpret_cast<const float4*>(Mt + j * kM + 4 * rg);
+            const float4 z = *reinterpret_cast<const float4*>(Zt + j * kZT + 4 * cg);
+            const float mv[4] = {m.x, m.y, m.z, m.w}, zv[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = fmaf(mv[ii], zv[kk], acc[ii][kk]);
+        }
+        const int k = k0 + 4 * cg;
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+            const int i = 4 * rg + ii;
+            const int row = i < n2 ? rid[i] : -1;
+            if (row >= 0 && k < c)
+                __stcg(reinterpret_cast<float4*>(Z + (size_t)row * ld + k),
+                       make_float4(acc[ii][0], acc[ii][1], acc[ii][2], acc[ii][3]));
+        }
     }
 }
 
@@ -581,52 +644,7 @@ __device__ int block_pair_reg(const RegCtx& C, float* W, float* Z, int ld, int c
     }
     if (lane == 0 && rot > 0) atomicOr(&s_any, 1);
     __syncthreads();
-    // U32 rows <- M U32 rows in column tiles of kZT staged in shared memory (the
-    // W rows are stored, so their space is free): thread (rg, cg) of 16 x 32
-    // computes rows 4 rg .. 4 rg + 3 and columns 4 cg .. 4 cg + 3 of the tile,
-    // reading M^T and the tile as float4
-    if (s_any) {
-        float* Zt = C.rows;              // [kM][kZT]
-        float* Mt = C.rows + kM * kZT;   // [kM][kM]: M transposed
-        for (int i = threadIdx.x; i < kM * kM; i += RT) Mt[(i % kM) * kM + i / kM] = C.M[i];
-        const int rg = threadIdx.x >> 5, cg = threadIdx.x & 31;
-        const int n2 = 2 * b;
-        for (int k0 = 0; k0 < c; k0 += kZT) {
-            __syncthreads();
-            for (int e = threadIdx.x; e < kM * (kZT / 4); e += RT) {
-                const int j = e / (kZT / 4), kk = 4 * (e % (kZT / 4));
-                const int row = j < n2 ? C.rid[j] : -1;
-                float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (row >= 0 && k0 + kk < c) v = __ldcg(reinterpret_cast<const float4*>(Z + (size_t)row * ld + k0 + kk));
-                *reinterpret_cast<float4*>(Zt + j * kZT + kk) = v;
-            }
-            __syncthreads();
-            float acc[4][4];
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = 0.0f;
-#pragma unroll 4
-            for (int j = 0; j < n2; ++j) {
-                const float4 m = *reinterpret_cast<const float4*>(Mt + j * kM + 4 * rg);
-                const float4 z = *reinterpret_cast<const float4*>(Zt + j * kZT + 4 * cg);
-                const float mv[4] = {m.x, m.y, m.z, m.w}, zv[4] = {z.x, z.y, z.z, z.w};
-#pragma unroll
-                for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) acc[ii][kk] = fmaf(mv[ii], zv[kk], acc[ii][kk]);
-            }
-            const int k = k0 + 4 * cg;
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii) {
-                const int i = 4 * rg + ii;
-                const int row = i < n2 ? C.rid[i] : -1;
-                if (row >= 0 && k < c)
-                    __stcg(reinterpret_cast<float4*>(Z + (size_t)row * ld + k),
-                           make_float4(acc[ii][0], acc[ii][1], acc[ii][2], acc[ii][3]));
-            }
-        }
-    }
+    if (s_any) apply_m_u32(C.M, C.rid, 2 * b, Z, ld, c, C.rows);
     __syncthreads();
     return rot;
 }
@@ -664,7 +682,8 @@ __device__ double kth_largest(const double* v, int c, int kk) {
 template <typename T>
 __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                        const int* group, unsigned* sync, int max_sweeps,
-                                                       double tol_in, unsigned long long timeout_ns, int ld) {
+                                                       double tol_in, unsigned long long timeout_ns, int ld,
+                                                       float pre_rho2) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool kF32 = sizeof(T) == 4;
     const int op = cta_op[blockIdx.x];
@@ -684,7 +703,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
         W = d.W;
         Z = d.transposed ? d.Z : nullptr;
     }
-    const int zl = Z ? c : 0;
+    const int zl = (!kF32 && Z) ? c : 0;   // FP32: U32 is turned per block pair, not staged
     // a block size that does not fit shared memory (or the registers) is a
     // planning error: every CTA of the op sees it and returns at once
     if (b < 1 || b > kMaxB ||
@@ -705,7 +724,10 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
     C.rowlen = L + zl;
     C.L = L;
     C.rows = reinterpret_cast<T*>(smem_raw);
-    C.nrm = C.rows + (size_t)2 * b * C.rowlen;
+    // the per-row data at a fixed offset past the rows' budget: the FP32
+    // path's U32 update stages its tiles over the rows (48 KB)
+    C.nrm = reinterpret_cast<T*>(smem_raw + kRowBytes);
+    C.M = (kF32 && !jacobi_f32_reg(L)) ? reinterpret_cast<float*>(smem_raw + kSmemBytes) : nullptr;
     C.dsc = reinterpret_cast<double*>(C.nrm + 2 * b);
     C.rid = reinterpret_cast<int*>(C.dsc + 2 * b);
     double* dscale = d.snorm + ld;   // FP64 pass: per-row scales (the QR's column norms are dead here)
@@ -856,7 +878,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                         if (ok) {
                             const T* w = W + (size_t)row * ld;
                             for (int k = lane; k < L; k += 32) dst[k] = __ldcg(w + k);
-                            if (Z)
+                            if (zl)
                                 for (int k = lane; k < c; k += 32) dst[L + k] = __ldcg(Z + (size_t)row * ld + k);
                             __syncwarp();
                             const T nv = (T)__ldcg(d.snorm + row);
@@ -871,8 +893,12 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                             C.rid[s] = -1;
                         }
                     }
+                    if (C.M)   // FP32 shared-memory path: the block pair's rotation starts at I
+                        for (int e = threadIdx.x; e < kMS * kMS; e += blockDim.x)
+                            C.M[e] = (e / kMS == e % kMS) ? 1.0f : 0.0f;
                     __syncthreads();
-                    rot += process_block_pair(C, b, r == 0, warp, lane);
+                    const int rot_bp = process_block_pair(C, b, r == 0, warp, lane);
+                    rot += rot_bp;
                     // store back
                     for (int s = warp; s < 2 * b; s += kWarps<T>) {
                         const int row = C.rid[s];
@@ -880,12 +906,16 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                         const T* src = C.rows + (size_t)s * C.rowlen;
                         T* w = W + (size_t)row * ld;
                         for (int k = lane; k < L; k += 32) __stcg(w + k, src[k]);
-                        if (Z)
+                        if (zl)
                             for (int k = lane; k < c; k += 32) __stcg(Z + (size_t)row * ld + k, src[L + k]);
                         if (lane == 0) {
                             __stcg(d.snorm + row, (double)C.nrm[s]);
                             if constexpr (!kF32) __stcg(dscale + row, C.dsc[s]);
                         }
+                    }
+                    if constexpr (kF32) {   // U32 rows of the pair turned by the accumulated rotation
+                        if (C.M && __syncthreads_or(rot_bp > 0))
+                            apply_m_u32(C.M, C.rid, 2 * b, Z, ld, c, reinterpret_cast<float*>(C.rows));
                     }
                     __syncthreads();
                 }
@@ -899,14 +929,15 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
             // FP32 pass: done when fewer than c/4 pairs still rotate (a few pairs
             // sit at FP32's resolution forever; the FP64 pass finishes them), or
             // when the largest relative off-orthogonality rotated away was at most
-            // 1e-3: the rows are then orthogonal to ~1e-6, FP32's rounding level
-            // for these inner products, and further sweeps only chase rounding.
+            // pre_rho (default 1e-3): the rows are then orthogonal to ~pre_rho^2,
+            // near FP32's rounding level for these inner products, and further
+            // sweeps only chase rounding.
             // FP64: no rotation, or the largest rotated rho had rho^2 <= 1e-6 tol: by
             // quadratic convergence the next sweep would meet pairs at ~rho^2, far
             // under tol, and rotate nothing (1e-20 for tol = sqrt(L) eps at L = 1024)
             if (threadIdx.x == 0)
                 s_conv = (ld_acquire(&sw[8 + sweep]) <= (kF32 ? (unsigned)(c / 4) : 0u)) ||
-                         (__uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= (kF32 ? 1e-6f : rho2_stop));
+                         (__uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + sweep])) <= (kF32 ? pre_rho2 : rho2_stop));
             __syncthreads();
             conv = s_conv;
             used = sweep + 1;
@@ -928,7 +959,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
             } else {
                 if (d.sweeps_out) *d.sweeps_out += used << 16;   // FP32 sweeps in the high half
                 if (d.pre_ok)
-                    *d.pre_ok = used > 0 && __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + used - 1])) <= 1e-6f;
+                    *d.pre_ok = used > 0 && __uint_as_float(ld_acquire(&sw[8 + kMaxSweepsCap + used - 1])) <= pre_rho2;
             }
         }
     }
@@ -940,6 +971,7 @@ timeout:
 }  // namespace
 
 size_t jacobi_sync_words_per_op() { return kSyncWords; }
+size_t jacobi_sync_words(int nops) { return (size_t)nops * kSyncWords; }
 
 
 cudaError_t jacobi_max_resident(int* blocks) {
@@ -964,11 +996,12 @@ cudaError_t jacobi_max_resident(int* blocks) {
 
 cudaError_t launch_jacobi(const OpDesc* d_desc, int nops, const int* d_cta_op, const int* d_cta_rank,
                           const int* d_group, unsigned* d_sync, int grid, int max_sweeps, double tol,
-                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st) {
+                          unsigned long long timeout_ns, int ld, bool fp32, cudaStream_t st, double pre_rho) {
     (void)nops;
     if (grid <= 0) return cudaSuccess;
+    float pre_rho2 = (float)(pre_rho * pre_rho);
     void* args[] = {(void*)&d_desc, (void*)&d_cta_op, (void*)&d_cta_rank, (void*)&d_group, (void*)&d_sync,
-                    (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld};
+                    (void*)&max_sweeps, (void*)&tol, (void*)&timeout_ns, (void*)&ld, (void*)&pre_rho2};
     const void* fn = fp32 ? (const void*)jacobi_kernel<float> : (const void*)jacobi_kernel<double>;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(fp32 ? kThreads<float> : kThreads<double>), args,
                                        fp32 ? kSmemF32 : kSmemBytes, st);

@@ -36,7 +36,7 @@ constexpr int QW = kQrWarps;   // warps per CTA
 constexpr int QT = QW * 32;
 constexpr int kMaxRowsQR = 4 * kMaxChi;
 
-__global__ void __launch_bounds__(QT, 4) qr_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
+__global__ void __launch_bounds__(QT, 1) qr_kernel(const OpDesc* descs, const int* cta_op, const int* cta_rank,
                                                    const int* group, unsigned* sync, unsigned long long timeout_ns,
                                                    int ld) {
     const int op = cta_op[blockIdx.x];
@@ -53,7 +53,6 @@ __global__ void __launch_bounds__(QT, 4) qr_kernel(const OpDesc* descs, const in
     const int gw = g * QW + warp, NW = G * QW;
     unsigned gen = 0;
     __shared__ int perm[kMaxRowsQR];   // logical column -> physical column (same in every CTA)
-    __shared__ double s_col[kMaxRowsQR];   // the pivot column of the current step, rows j .. m-1
     __shared__ double s_v0, s_beta;
     __shared__ double s_best[QW];
     __shared__ int s_bidx[QW];
@@ -109,19 +108,13 @@ __global__ void __launch_bounds__(QT, 4) qr_kernel(const OpDesc* descs, const in
             }
             __syncthreads();
         }
-        // the pivot column into shared memory: every warp of the CTA reads it
-        // for each of its trailing columns
-        {
-            const double* col = A + (size_t)perm[j] * ld;
-            for (int i = j + threadIdx.x; i < m; i += QT) s_col[i] = __ldcg(col + i);
-        }
-        __syncthreads();
+        const double* col = A + (size_t)perm[j] * ld;
         if (warp == 0) {
             double ss = 0.0;
-            for (int i = j + 1 + lane; i < m; i += 32) ss = fma(s_col[i], s_col[i], ss);
+            for (int i = j + 1 + lane; i < m; i += 32) ss = fma(__ldcg(col + i), __ldcg(col + i), ss);
             ss = warp_sum(ss);
             if (lane == 0) {
-                const double x0 = s_col[j];
+                const double x0 = __ldcg(col + j);
                 const double nrm = sqrt(fma(x0, x0, ss));
                 const double alpha = x0 > 0.0 ? -nrm : nrm;
                 s_v0 = x0 - alpha;
@@ -136,31 +129,12 @@ __global__ void __launch_bounds__(QT, 4) qr_kernel(const OpDesc* descs, const in
             const int pk = perm[k];
             double* y = A + (size_t)pk * ld;
             if (beta != 0.0) {
-                // w = v . y with four loads in flight per lane, then y -= beta w v
-                double w0 = 0.0, w1 = 0.0, w2 = 0.0, w3 = 0.0;
-                int i = j + 1 + lane;
-                for (; i + 96 < m; i += 128) {
-                    const double y0 = __ldcg(y + i), y1 = __ldcg(y + i + 32), y2 = __ldcg(y + i + 64),
-                                 y3 = __ldcg(y + i + 96);
-                    w0 = fma(s_col[i], y0, w0);
-                    w1 = fma(s_col[i + 32], y1, w1);
-                    w2 = fma(s_col[i + 64], y2, w2);
-                    w3 = fma(s_col[i + 96], y3, w3);
-                }
-                for (; i < m; i += 32) w0 = fma(s_col[i], __ldcg(y + i), w0);
-                double w = warp_sum((w0 + w1) + (w2 + w3));
+                double w = 0.0;
+                for (int i = j + 1 + lane; i < m; i += 32) w = fma(__ldcg(col + i), __ldcg(y + i), w);
+                w = warp_sum(w);
                 w = fma(v0, __ldcg(y + j), w);
                 const double s = beta * w;
-                i = j + 1 + lane;
-                for (; i + 96 < m; i += 128) {
-                    const double y0 = __ldcg(y + i), y1 = __ldcg(y + i + 32), y2 = __ldcg(y + i + 64),
-                                 y3 = __ldcg(y + i + 96);
-                    __stcg(y + i, fma(-s, s_col[i], y0));
-                    __stcg(y + i + 32, fma(-s, s_col[i + 32], y1));
-                    __stcg(y + i + 64, fma(-s, s_col[i + 64], y2));
-                    __stcg(y + i + 96, fma(-s, s_col[i + 96], y3));
-                }
-                for (; i < m; i += 32) __stcg(y + i, fma(-s, s_col[i], __ldcg(y + i)));
+                for (int i = j + 1 + lane; i < m; i += 32) __stcg(y + i, fma(-s, __ldcg(col + i), __ldcg(y + i)));
                 if (lane == 0) __stcg(y + j, fma(-s, v0, __ldcg(y + j)));
                 __syncwarp();
             }

@@ -53,11 +53,11 @@ int time_jacobi(mpdo_ctx* c, std::vector<OpDesc>& h, bool fp32, int b, double* m
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words_per_op() * nops, c->st));
+    CU(cudaMemsetAsync(c->d_sync, 0, sizeof(unsigned) * jacobi_sync_words(nops), c->st));
     CU(cudaEventRecord(e0, c->st));
     CU(launch_jacobi(c->d_desc, nops, c->d_cta, c->d_cta + total, c->d_cta + 2 * total, c->d_sync, total,
                      fp32 ? kMaxSweepsCap / 2 : c->cfg.jacobi_max_sweeps, fp32 ? 0.0 : fp64_jacobi_tol(c), timeout_ns, ld,
-                     fp32, c->st));
+                     fp32, c->st, precond_rho(c)));
     CU(cudaEventRecord(e1, c->st));
     CU(cudaEventSynchronize(e1));
     float ms = 0.0f;

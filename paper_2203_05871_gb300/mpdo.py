@@ -34,7 +34,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("storage", ctypes.c_int), ("trotter_order", ctypes.c_int),
                 ("force_trace", ctypes.c_int), ("jacobi_max_sweeps", ctypes.c_int),
                 ("jacobi_tol", ctypes.c_double), ("barrier_timeout_ms", ctypes.c_uint),
-                ("max_slots", ctypes.c_int), ("device", ctypes.c_int), ("qr_blocked", ctypes.c_int)]
+                ("max_slots", ctypes.c_int), ("device", ctypes.c_int), ("qr_blocked", ctypes.c_int),
+                ("precond_rho", ctypes.c_double)]
 
 
 class Model(ctypes.Structure):
@@ -181,7 +182,8 @@ class Solver:
     def __init__(self, n_qubits: int, batch: int = 1, chi_cap: int = 32, precision: int = FP64,
                  storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 100,
                  jacobi_tol: float = 0.0, barrier_timeout_ms: int = 4000, max_slots: int = 0,
-                 device: Optional[int] = None, trotter_order: int = 2, qr_blocked: bool = False):
+                 device: Optional[int] = None, trotter_order: int = 2, qr_blocked: bool = False,
+                 precond_rho: float = 0.0):
         lib = load_library()
         cfg = Config()
         _check(lib.mpdo_config_default(ctypes.byref(cfg)))
@@ -192,6 +194,7 @@ class Solver:
         cfg.barrier_timeout_ms, cfg.max_slots = barrier_timeout_ms, max_slots
         cfg.trotter_order = int(trotter_order)
         cfg.qr_blocked = 1 if qr_blocked else 0
+        cfg.precond_rho = float(precond_rho)
         if device is None:
             try:
                 import torch
