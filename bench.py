@@ -570,7 +570,7 @@ def truncation_roofline(prof, precision):
     ms = sum(prof[k]["ms"] for k in parts)
     achieved = jac["flops"] / (ms / 1e3) / 1e12 if ms > 0 else None
     names = {"qr": "qr_kernel", "jacobi_svd": "jacobi_kernel<double>", "jacobi_fp32": "jacobi_kernel<float>",
-             "precond_gemm": "gemm_kernel x3"}
+             "precond_gemm": "oz_prep/slice/gemm kernels x3 (preconditioner products)"}
     return {"kernel": "truncation stage: " + " + ".join(names[k] for k in parts),
             "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_NOMINAL_TFLOPS, "unit": "TFLOP/s",
             "frac": (achieved / FP64_PEAK_NOMINAL_TFLOPS) if achieved else None,
@@ -578,7 +578,9 @@ def truncation_roofline(prof, precision):
             "note": "achieved = 21 n^3 flops per n x n SVD (n = 4 max(chi_l, chi_r)), the FP64 work of an ideal "
                     "Golub-Kahan SVD, over the summed CUDA-event time of the listed kernels (QR included); peak = "
                     "nominal FP64 of GB300 (2 DFMA/SM/clk x 152 SMs x 2.07 GHz; MEASURED_PEAKS.json has no "
-                    "FP64 figure), of nominal; traffic: not re-captured for these kernels"}
+                    "FP64 figure), of nominal; traffic: null, the stage is several kernels whose rows stay in "
+                    "L2 (a jacobi_kernel<double> launch of the chain10_chi256 case read 2.8 MB of DRAM, "
+                    "profiles/kernels_chain10_chi256.md)"}
 
 
 def main():
