@@ -66,6 +66,7 @@ constexpr int kThreads = kWarps<T> * 32;
 constexpr int kRowBytes = kJacobiRowBytes;             // two blocks of rows in shared memory
 constexpr int kMaxB = kJacobiMaxB;
 constexpr int kSmemBytes = kRowBytes + 6 * kMaxB * 8;  // rows + norms (2b) + scales (2b) + row ids
+constexpr int kSwQueue = 2;   // per-op sync words 2, 3: the block-pair counters of alternate rounds
 constexpr double kScaleFloor = 0x1p-32;   // FP64 row scales below this are multiplied into the row
 
 __device__ __forceinline__ int tour_player(int x, int step, int cp) {
@@ -719,6 +720,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
     __shared__ double s_floor2, s_scale;
     __shared__ int s_conv;
     __shared__ unsigned s_rho2;
+    __shared__ int s_pair;
 
     Ctx<T> C;
     C.rowlen = L + zl;
@@ -851,7 +853,20 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                 __syncthreads();
             }
             for (int r = 0; r < nbp - 1; ++r) {
-                for (int i = g; i < npair; i += G) {
+                // The block pairs of a round go to the op's CTAs through a shared
+                // counter, so that a CTA whose pairs are cheap (both blocks
+                // discarded, or already orthogonal) takes more of them instead
+                // of waiting at the round's barrier.  Two counters alternate by
+                // round; the one of the next round is cleared in this one (every
+                // CTA is past its last use: the barrier ending the previous round).
+                const unsigned rg = (unsigned)(sweep * (nbp - 1) + r);
+                if (g == 0 && threadIdx.x == 0) atomicExch(&sw[kSwQueue + ((rg + 1) & 1)], 0u);
+                for (;;) {
+                    if (threadIdx.x == 0) s_pair = (int)atomicAdd(&sw[kSwQueue + (rg & 1)], 1u);
+                    __syncthreads();
+                    const int i = s_pair;
+                    __syncthreads();   // read by all before thread 0 takes the next one
+                    if (i >= npair) break;
                     const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
                     const int bl[2] = {P < Q ? P : Q, P < Q ? Q : P};
                     if constexpr (kF32) {
