@@ -8,8 +8,10 @@
 
 namespace mpdo {
 
-// per-op sync words: [0] barrier arrivals, [1] abort flag, [8 + s] rotations in Jacobi sweep s
-constexpr int kSyncWords = 8 + 2 * kMaxSweepsCap;   // flags, rotations per sweep, largest off-orthogonality per sweep
+// per-op sync words: [0] barrier arrivals, [1] abort flag, [2, 8) Jacobi pair counters,
+// [8 + s] rotations and [8 + kMaxSweepsCap + s] largest off-orthogonality in Jacobi
+// sweep s, then one version per Jacobi row block (at most 4 kMaxChi blocks)
+constexpr int kSyncWords = 8 + 2 * kMaxSweepsCap + 4 * kMaxChi;
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;

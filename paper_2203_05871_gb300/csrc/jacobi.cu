@@ -13,8 +13,10 @@
 // blocks once per sweep; in a round each CTA loads one or more block pairs
 // into shared memory, rotates every cross pair of rows (and, in the first
 // round of a sweep, every pair inside each block), and stores the blocks back
-// to their home rows.  One barrier per round orders the CTAs of an op; every
-// wait is bounded by a wall-clock limit after which the kernel records
+// to their home rows.  The op's CTAs take the block pairs of a sweep from a
+// shared counter in round order, and a pair waits only for its two blocks to
+// leave the previous round (a version per block); one barrier per sweep.
+// Every wait is bounded by a wall-clock limit after which the kernel records
 // MPDO_ST_TIMEOUT and returns.  The launch is cooperative (all CTAs resident).
 // Within a block pair one warp owns one pair of rows: the inner product is
 // reduced with warp shuffles, the rotation is applied in shared memory.
@@ -66,7 +68,32 @@ constexpr int kThreads = kWarps<T> * 32;
 constexpr int kRowBytes = kJacobiRowBytes;             // two blocks of rows in shared memory
 constexpr int kMaxB = kJacobiMaxB;
 constexpr int kSmemBytes = kRowBytes + 6 * kMaxB * 8;  // rows + norms (2b) + scales (2b) + row ids
-constexpr int kSwQueue = 2;   // per-op sync words 2, 3: the block-pair counters of alternate rounds
+constexpr int kSwQueue = 2;   // per-op sync words 2, 3: the block-pair counters of alternate sweeps
+constexpr int kSwVer = 8 + 2 * kMaxSweepsCap;   // per-op sync words: one version per row block
+static_assert(kSwVer + 4 * kMaxChi <= kSyncWords, "a version for every row block");
+
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait (thread 0) until row blocks P and Q (those < nb) have left round R - 1,
+// i.e. their versions reached R; bounded by timeout_ns, after which the op's
+// abort flag is raised.  Returns 0 if it gave up.
+__device__ int wait_blocks(const unsigned* ver, int P, int Q, int nb, unsigned R, unsigned* abort_flag,
+                           unsigned long long timeout_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        const bool okP = P >= nb || ld_acquire(ver + P) >= R;
+        const bool okQ = Q >= nb || ld_acquire(ver + Q) >= R;
+        if (okP && okQ) return 1;
+        if (ld_acquire(abort_flag) != 0u) return 0;
+        if (globaltimer_ns() - t0 > timeout_ns) {
+            atomicExch(abort_flag, 1u);
+            return 0;
+        }
+        __nanosleep(32);
+    }
+}
 constexpr double kScaleFloor = 0x1p-32;   // FP64 row scales below this are multiplied into the row
 
 __device__ __forceinline__ int tour_player(int x, int step, int cp) {
@@ -852,27 +879,34 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                 if (s_conv && C.thr == 0.0) C.thr = kth_largest(d.snorm, c, d.chi_max + max(16, d.chi_max / 8));
                 __syncthreads();
             }
-            for (int r = 0; r < nbp - 1; ++r) {
-                // The block pairs of a round go to the op's CTAs through a shared
-                // counter, so that a CTA whose pairs are cheap (both blocks
-                // discarded, or already orthogonal) takes more of them instead
-                // of waiting at the round's barrier.  Two counters alternate by
-                // round; the one of the next round is cleared in this one (every
-                // CTA is past its last use: the barrier ending the previous round).
-                const unsigned rg = (unsigned)(sweep * (nbp - 1) + r);
-                if (g == 0 && threadIdx.x == 0) atomicExch(&sw[kSwQueue + ((rg + 1) & 1)], 0u);
-                for (;;) {
-                    if (threadIdx.x == 0) s_pair = (int)atomicAdd(&sw[kSwQueue + (rg & 1)], 1u);
-                    __syncthreads();
-                    const int i = s_pair;
-                    __syncthreads();   // read by all before thread 0 takes the next one
-                    if (i >= npair) break;
-                    const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
-                    const int bl[2] = {P < Q ? P : Q, P < Q ? Q : P};
+            // The block pairs of a sweep go to the op's CTAs through a shared
+            // counter (position q: round q / npair, pair q % npair), and a round
+            // has no barrier: a pair waits only until its two blocks have left
+            // the previous round (a version per block).  A CTA whose pairs are
+            // cheap (both blocks discarded, or already orthogonal) takes more of
+            // them, and a round starts where its blocks are ready.  Positions are
+            // taken in order, so the pairs a CTA waits for are held by CTAs that
+            // can progress.  Two counters alternate by sweep; the next one is
+            // cleared during this sweep (every CTA is past its last use).
+            if (g == 0 && threadIdx.x == 0) atomicExch(&sw[kSwQueue + ((sweep + 1) & 1)], 0u);
+            for (;;) {
+                if (threadIdx.x == 0) s_pair = (int)atomicAdd(&sw[kSwQueue + (sweep & 1)], 1u);
+                __syncthreads();
+                const int qpos = s_pair;
+                __syncthreads();   // read by all before thread 0 takes the next one
+                if (qpos >= (nbp - 1) * npair) break;
+                const int r = qpos / npair, i = qpos % npair;
+                const int P = tour_player(i, r, nbp), Q = tour_player(nbp - 1 - i, r, nbp);
+                const unsigned R = (unsigned)(sweep * (nbp - 1) + r);   // rounds of this launch before
+                if (threadIdx.x == 0) s_conv = wait_blocks(sw + kSwVer, P, Q, nb, R, &sw[1], timeout_ns);
+                __syncthreads();
+                if (!s_conv) goto timeout;
+                const int bl[2] = {P < Q ? P : Q, P < Q ? Q : P};
+                do {
                     if constexpr (kF32) {
                         if (reg) {
                             rot += block_pair_reg(RC, W, Z, ld, c, nb, bl, r == 0, d.snorm, warp, lane);
-                            continue;
+                            break;
                         }
                     }
                     if constexpr (!kF32) {   // both blocks discarded: nothing to do
@@ -882,7 +916,7 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                             const int row = blk * b + (threadIdx.x % b);
                             if (blk < nb && row < c) pred = __ldcg(d.snorm + row) < C.thr;
                         }
-                        if (__syncthreads_and(pred)) continue;
+                        if (__syncthreads_and(pred)) break;
                     }
                     // load the two blocks (slot s < b: block bl[0]; s >= b: block bl[1])
                     for (int s = warp; s < 2 * b; s += kWarps<T>) {
@@ -933,14 +967,19 @@ __global__ void __launch_bounds__(kThreads<T>, 1) jacobi_kernel(const OpDesc* de
                             apply_m_u32(C.M, C.rid, 2 * b, Z, ld, c, reinterpret_cast<float*>(C.rows));
                     }
                     __syncthreads();
+                } while (false);
+                // the pair's rows (and U32 rows) are stored: its blocks leave round r
+                __threadfence();
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    if (P < nb) st_release(&sw[kSwVer + P], R + 1);
+                    if (Q < nb) st_release(&sw[kSwVer + Q], R + 1);
                 }
-                if (r == nbp - 2) {
-                    if (lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
-                    __syncthreads();
-                    if (threadIdx.x == 0 && s_rho2) atomicMax(&sw[8 + kMaxSweepsCap + sweep], s_rho2);
-                }
-                if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             }
+            if (lane == 0 && rot > 0) atomicAdd(&sw[8 + sweep], (unsigned)rot);
+            __syncthreads();
+            if (threadIdx.x == 0 && s_rho2) atomicMax(&sw[8 + kMaxSweepsCap + sweep], s_rho2);
+            if (!op_barrier(sw, G, gen, timeout_ns)) goto timeout;
             // FP32 pass: done when fewer than c/4 pairs still rotate (a few pairs
             // sit at FP32's resolution forever; the FP64 pass finishes them), or
             // when the largest relative off-orthogonality rotated away was at most
