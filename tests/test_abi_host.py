@@ -74,3 +74,8 @@ def test_init_rejects_bad_config_without_gpu(lib):
     assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
     cfg.chi_cap, cfg.trotter_order = 16, 3
     assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
+    cfg.trotter_order = 2
+    for bad in (2.0, float("nan")):
+        cfg.precond_rho = bad
+        assert lib.mpdo_init(ctypes.byref(h), ctypes.byref(cfg), None) == mpdo.MPDO_EINVAL
+        assert "precond_rho" in lib.mpdo_last_error().decode()
