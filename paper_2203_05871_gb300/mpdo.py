@@ -177,7 +177,17 @@ def _ptr(a, ctype):
 
 
 class Solver:
-    """One libmpdo context: B instances of an N-qubit model on one GPU."""
+    """One libmpdo context: B instances of an N-qubit model on one GPU.
+
+    The keyword arguments fill ``mpdo_config`` (include/mpdo.h documents each
+    field): ``precision`` FP64, MIXED_TF32 or MIXED_BF16X3; ``storage``
+    STORE_F64 or STORE_F32; ``trotter_order`` 2 or 4; ``jacobi_tol`` and
+    ``jacobi_max_sweeps`` of the SVD; ``barrier_timeout_ms`` bounding every
+    device-side wait; ``max_slots`` (ops in flight, 0 = automatic);
+    ``qr_blocked`` (mixed path: the blocked QR instead of the column QR);
+    ``precond_rho`` (mixed path: the FP32 preconditioning sweeps' stop
+    threshold, 0 = 1e-3); ``stream`` a torch stream or a raw cudaStream_t.
+    """
 
     def __init__(self, n_qubits: int, batch: int = 1, chi_cap: int = 32, precision: int = FP64,
                  storage: int = STORE_F64, stream=None, force_trace: bool = True, jacobi_max_sweeps: int = 100,
