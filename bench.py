@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=1,
                     help="timed steps of the 64-instance batched workload (0: skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-ops", type=int, default=5, help="timed oracle ops of cpu_baseline")
+    ap.add_argument("--cpu-ops", type=int, default=5, help="timed oracle ops of every op shape in cpu_baseline")
     ap.add_argument("--no-cpu-plain", action="store_true", help="skip the plain C Jacobi op")
     ap.add_argument("--oracle-svd", default="lapack", choices=["lapack", "jacobi"],
                     help="SVD route of --impl reference")
